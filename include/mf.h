@@ -1,0 +1,183 @@
+/* mf.h -- C ABI of the B300 matrix-free rotor-stator operator library (libmf.so).
+ *
+ * The library evaluates, on one GPU, the discrete operator of "High-order
+ * stabilized matrix-free simulation of rotating mixing devices using the Mortar
+ * Element Method":
+ *   - the stabilised ALE incompressible Navier-Stokes residual F-hat*_NS
+ *     (Eqs. EqNS, Eq-NSweakWmortar, Eq-NSweakComplete, Eq-strong-residual,
+ *     Eq-stab-param) on continuous Q_k quadrilaterals (d = 2) or hexahedra
+ *     (d = 3) with equal-order velocity/pressure (Eq. Eq-shape-functions);
+ *   - its Newton Jacobian (blocks A-hat..D-hat, Section 2.3; tau frozen);
+ *   - the Nitsche/SIPG mortar face terms coupling the rotating rotor to the
+ *     stator (Eqs. EqMortarPre, EqMortarDiff, EqPenalty, EqMortarMass) on mortar
+ *     cells built from both angular partitions of the interface (Section 3.2),
+ *     with the rotor rotated rigidly (Section 3.1);
+ *   - a Newton / flexible-GMRES solve of one nonlinear step (Eq.
+ *     Eq-Newton-method) with Jacobi, Chebyshev-Jacobi (FP32 or FP64) smoothing.
+ *
+ * Conventions
+ *   - Vectors are interleaved per node: [node][u_1 .. u_d, p] (d+1 values per
+ *     node), in the mesh's node numbering.  Interface nodes are duplicated: the
+ *     rotor copy and the stator copy are different nodes.
+ *   - Unless stated otherwise, every pointer argument of an operator call is
+ *     caller-owned DEVICE memory on the current CUDA device; the library keeps
+ *     no caller pointer past the call.  Calls are asynchronous on `stream`
+ *     (a cudaStream_t passed as void*, NULL = legacy default stream), except
+ *     those documented as synchronising.
+ *   - Velocity components on wall nodes carry homogeneous (or mf_dirichlet)
+ *     Dirichlet conditions: Jacobian rows/columns there are identity and the
+ *     residual there is u - g.  Pressure is unconstrained (the constant
+ *     pressure is a near null vector; solves remove the pressure mean).
+ *   - Every call returns an mf_status; on failure mf_last_error(h) holds a
+ *     message.  No call throws across the ABI.
+ */
+#ifndef MF_H
+#define MF_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mf_ctx* mf_handle;
+typedef struct mf_mesh mf_mesh;
+
+typedef enum {
+  MF_OK = 0,
+  MF_ERR_ARG = 1,          /* invalid argument (null pointer, size, range) */
+  MF_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  MF_ERR_OOM = 3,          /* device allocation failed */
+  MF_ERR_STATE = 4,        /* call out of order (e.g. apply before set_linearization) */
+  MF_ERR_NAN = 5,          /* non-finite value met by a solve */
+  MF_ERR_NOT_CONVERGED = 6,/* solve stopped at its iteration limit above tolerance */
+  MF_ERR_BREAKDOWN = 7,    /* Krylov breakdown (zero Arnoldi vector before convergence) */
+  MF_ERR_ITER_LIMIT = 8    /* reserved: device-side loop hit its hard cap */
+} mf_status;
+
+typedef enum { MF_FP64 = 0, MF_FP32 = 1 } mf_precision;
+
+/* ---------------------------------------------------------------- mesh
+ * mf_mesh_from_arrays: copy a merged rotor-stator mesh from HOST arrays.
+ *   d            2 or 3
+ *   k            polynomial degree of the Q_k geometry/solution nodes (1..5)
+ *   n_nodes, x0  [n_nodes][d] node coordinates in the reference (theta = 0)
+ *                configuration
+ *   node_side    [n_nodes] 0 = rotor node (rotates), 1 = stator node
+ *   wall         [n_nodes] 1 = velocity Dirichlet node
+ *   n_cells, cells [n_cells][(k+1)^d] int32 node ids, tensor order with xi_0
+ *                fastest; every cell map must have positive Jacobian
+ *   cell_side    [n_cells] 0 = rotor cell (mesh velocity omega e_z x x), 1 = stator
+ *   R, n_R, n_z, H, phi0  circular interface r = R about the z axis with n_R
+ *                equal cells per z-layer on each side (the paper's restriction,
+ *                Section 3.1), n_z layers of height H/n_z (d = 3; n_z = 1 and H
+ *                ignored in 2D); at theta = 0 both partitions start at angle phi0
+ *   iface_rotor, iface_stator  [n_z][n_R] cell ids: entry (l, j) is the cell
+ *                of z-layer l spanning angles [phi0 + j D, phi0 + (j+1) D],
+ *                D = 2 pi / n_R, at theta = 0.  Interface cells are oriented
+ *                xi_0 radial outward, xi_1 counter-clockwise angle, xi_2 = z;
+ *                the interface face is xi_0 = 1 (rotor) / xi_0 = 0 (stator).
+ * The library copies everything; the caller may free its arrays on return.
+ * Errors: MF_ERR_ARG for null pointers, d/k out of range, ids out of range.
+ */
+mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const double* x0,
+                              const uint8_t* node_side, const uint8_t* wall,
+                              int64_t n_cells, const int32_t* cells, const uint8_t* cell_side,
+                              double R, int n_R, int n_z, double H, double phi0,
+                              const int32_t* iface_rotor, const int32_t* iface_stator,
+                              mf_mesh** out);
+void mf_mesh_free(mf_mesh* m);
+
+/* ---------------------------------------------------------------- options */
+typedef struct {
+  double penalty_F;   /* F of Eq. EqPenalty (default 1) */
+  int    reserved[8];
+} mf_options;
+
+/* mf_create: set up the operator on the current CUDA device (synchronising).
+ *   k must equal the mesh degree; nu >= 0 kinematic viscosity; omega rotor
+ *   angular velocity about e_z; dt > 0 time step of BDF order bdf (1|2), or
+ *   dt = 0 for the steady operator (time terms and the (1/dt)^2 part of tau
+ *   dropped).  opt may be NULL (defaults).  The rotor starts at theta = 0.
+ * Errors: MF_ERR_ARG (bad parameters), MF_ERR_OOM, MF_ERR_CUDA. */
+mf_status mf_create(const mf_mesh* m, int k, double nu, double omega, double dt, int bdf,
+                    const mf_options* opt, mf_handle* out);
+mf_status mf_destroy(mf_handle h);
+const char* mf_last_error(mf_handle h);
+mf_status mf_sizes(mf_handle h, int64_t* n_nodes, int64_t* n_dofs, int64_t* n_cells,
+                   int64_t* n_mortar_cells);
+
+/* Rotor angle (Section 3.1 rotation, Section 3.2 mortar cells): rotates the
+ * rotor nodes to x = R(theta) x0 and rebuilds the mortar points.  Called by
+ * mf_set_linearization; exposed for drivers that move the rotor alone. */
+mf_status mf_set_angle(mf_handle h, double theta, void* stream);
+
+/* Current node coordinates, device out [n_nodes][d]. */
+mf_status mf_node_coords(mf_handle h, double* xyz_out, void* stream);
+
+/* Dirichlet values g (device [n_nodes][d], read at wall nodes), NULL = zero. */
+mf_status mf_dirichlet(mf_handle h, const double* g, void* stream);
+
+/* BDF history (device [n_nodes][d] each; u_nm1 ignored/NULL for BDF1):
+ * stores h_t = (alpha_1 u^n + alpha_2 u^{n-1}) / dt. */
+mf_status mf_set_history(mf_handle h, const double* u_n, const double* u_nm1, void* stream);
+
+/* Linearisation state (device [n_nodes][d+1] FP64) at rotor angle theta:
+ * rotates, remaps the mortar, and caches per Gauss point the geometry and the
+ * frozen-tau linearisation (advection u*-u_ALE, grad u*, strong residual R*,
+ * tau) in FP64 and an FP32 copy.  Must precede mf_apply_jacobian/mf_diagonal. */
+mf_status mf_set_linearization(mf_handle h, const double* up_star, double theta, void* stream);
+
+/* Residual r = F-hat*_NS(up) (volume + mortar terms, FP64), r = u - g on wall
+ * velocity DoFs.  up, r: device [n_nodes][d+1] FP64; tau from up itself. */
+mf_status mf_residual(mf_handle h, const double* up, double* r, void* stream);
+
+/* y = J x at the current linearisation.  prec MF_FP64: x, y double; MF_FP32:
+ * x, y float (FP32 cache).  x entries on wall velocity DoFs are ignored as
+ * inputs and copied to y (identity rows/columns).  x and y must not alias. */
+mf_status mf_apply_jacobian(mf_handle h, const void* x, void* y, mf_precision prec, void* stream);
+
+/* diag(J) at the current linearisation (volume and mortar parts, Algorithm 1;
+ * 1 on wall velocity DoFs), device [n_nodes][d+1] of the given precision. */
+mf_status mf_diagonal(mf_handle h, void* diag_out, mf_precision prec, void* stream);
+
+/* ---------------------------------------------------------------- solve */
+typedef enum { MF_PC_JACOBI = 0, MF_PC_CHEBYSHEV = 1 } mf_pc_kind;
+
+typedef struct {
+  double newton_rtol;   /* stop when ||R||_2 <= newton_rtol ||R_0||_2 (default 1e-8) */
+  double newton_atol;   /* or ||R||_2 <= newton_atol (default 0) */
+  int    max_newton;    /* default 20 */
+  double lin_rtol;      /* FGMRES relative tolerance per Newton step (default 1e-4) */
+  int    restart;       /* FGMRES restart length (default 50, max 200) */
+  int    max_lin_iters; /* total FGMRES iterations per Newton step (default 500) */
+  int    pc;            /* mf_pc_kind (default MF_PC_CHEBYSHEV) */
+  int    pc_precision;  /* mf_precision of the preconditioner applies (default MF_FP32) */
+  int    cheb_degree;   /* Chebyshev degree (default 4) */
+  double cheb_lo;       /* lower end of the Chebyshev interval as a fraction of lambda_max (default 0.1) */
+  double theta;         /* rotor angle of this step */
+} mf_solver_opts;
+
+typedef struct {
+  int    newton_iters;
+  int    lin_iters_total;
+  int    lin_iters[64];       /* per Newton step (first 64) */
+  double res_norm[65];        /* ||R||_2 before each Newton step and at exit */
+  double lambda_max;          /* estimated spectral radius of D^-1 J */
+  double seconds;             /* wall time of the solve (host clock) */
+  int    status;              /* mf_status of the solve */
+} mf_solve_report;
+
+void mf_solver_defaults(mf_solver_opts* o);
+
+/* One nonlinear step: Newton on R(up) = 0 at angle so->theta, each linear
+ * system by right-preconditioned FGMRES with FP64 residual, Jacobian applies
+ * and CGS2 orthogonalisation.  up: device [n_nodes][d+1] FP64, in: initial
+ * guess, out: solution.  Synchronising (reads convergence data back);
+ * rep (host) may be NULL.  Returns MF_ERR_NOT_CONVERGED / MF_ERR_BREAKDOWN /
+ * MF_ERR_NAN on failure (up then holds the last iterate). */
+mf_status mf_solve_step(mf_handle h, double* up, const mf_solver_opts* so, mf_solve_report* rep,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

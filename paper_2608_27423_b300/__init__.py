@@ -1,0 +1,130 @@
+"""B300 matrix-free rotor-stator operator (stabilised ALE Navier-Stokes + Nitsche/SIPG mortar).
+
+Thin Python binding over ``libmf.so`` (C ABI in ``include/mf.h``).  Device
+memory and streams come from PyTorch; every arithmetic step runs in the CUDA
+library.  There is no CPU fallback: calls raise if the library is missing.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import MF_FP64, MF_FP32, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MfError, MfSolverOpts, MfSolveReport
+
+__all__ = ["RotorStatorOperator", "MF_FP64", "MF_FP32", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MfError",
+           "solver_defaults"]
+
+
+def _check(status, h=None, what=""):
+    if status != 0:
+        lib = _lib.load()
+        msg = lib.mf_last_error(h).decode() if h else ""
+        name = _lib.STATUS_NAMES[status] if 0 <= status < len(_lib.STATUS_NAMES) else str(status)
+        err = MfError(f"{what}: {name} {msg}")
+        err.status = status
+        raise err
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def solver_defaults(**over):
+    o = MfSolverOpts()
+    _lib.load().mf_solver_defaults(C.byref(o))
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+class RotorStatorOperator:
+    """One operator instance on the current CUDA device.
+
+    mesh: object with d, k, x0, node_side, wall, cells, cell_side, R, n_R, n_z,
+    H, phi0, iface_rotor, iface_stator (e.g. synth.RotorStatorMesh).
+    """
+
+    def __init__(self, mesh, nu, omega, dt, bdf, penalty_F=1.0):
+        lib = _lib.load()
+        self.lib = lib
+        self.d, self.k = int(mesh.d), int(mesh.k)
+        x0 = np.ascontiguousarray(mesh.x0, dtype=np.float64)
+        ns = np.ascontiguousarray(mesh.node_side, dtype=np.uint8)
+        wall = np.ascontiguousarray(mesh.wall, dtype=np.uint8)
+        cells = np.ascontiguousarray(mesh.cells, dtype=np.int32)
+        cs = np.ascontiguousarray(mesh.cell_side, dtype=np.uint8)
+        ifr = np.ascontiguousarray(mesh.iface_rotor, dtype=np.int32)
+        ifs = np.ascontiguousarray(mesh.iface_stator, dtype=np.int32)
+        mp = C.c_void_p()
+        _check(lib.mf_mesh_from_arrays(self.d, self.k, x0.shape[0], _np_ptr(x0), _np_ptr(ns), _np_ptr(wall),
+                                       cells.shape[0], _np_ptr(cells), _np_ptr(cs), float(mesh.R), int(mesh.n_R),
+                                       int(mesh.n_z), float(mesh.H), float(mesh.phi0), _np_ptr(ifr), _np_ptr(ifs),
+                                       C.byref(mp)), None, "mf_mesh_from_arrays")
+        opt = _lib.MfOptions()
+        opt.penalty_F = penalty_F
+        hp = C.c_void_p()
+        st = lib.mf_create(mp, self.k, float(nu), float(omega), float(dt), int(bdf), C.byref(opt), C.byref(hp))
+        lib.mf_mesh_free(mp)
+        _check(st, None, "mf_create")
+        self.h = hp
+        nn, nd, nc, nm = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib.mf_sizes(hp, C.byref(nn), C.byref(nd), C.byref(nc), C.byref(nm)), hp, "mf_sizes")
+        self.n_nodes, self.n_dofs, self.n_cells, self.n_mortar = nn.value, nd.value, nc.value, nm.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st, what):
+        _check(st, self.h, what)
+
+    def set_angle(self, theta, stream=None):
+        self._chk(self.lib.mf_set_angle(self.h, float(theta), _stream(stream)), "mf_set_angle")
+
+    def node_coords(self, out, stream=None):
+        self._chk(self.lib.mf_node_coords(self.h, _ptr(out), _stream(stream)), "mf_node_coords")
+
+    def set_dirichlet(self, g=None, stream=None):
+        self._chk(self.lib.mf_dirichlet(self.h, _ptr(g) if g is not None else None, _stream(stream)),
+                  "mf_dirichlet")
+
+    def set_history(self, u_n, u_nm1=None, stream=None):
+        self._chk(self.lib.mf_set_history(self.h, _ptr(u_n), _ptr(u_nm1) if u_nm1 is not None else None,
+                                          _stream(stream)), "mf_set_history")
+
+    def set_linearization(self, up_star, theta, stream=None):
+        self._chk(self.lib.mf_set_linearization(self.h, _ptr(up_star), float(theta), _stream(stream)),
+                  "mf_set_linearization")
+
+    def residual(self, up, r, stream=None):
+        self._chk(self.lib.mf_residual(self.h, _ptr(up), _ptr(r), _stream(stream)), "mf_residual")
+
+    def apply_jacobian(self, x, y, prec=MF_FP64, stream=None):
+        self._chk(self.lib.mf_apply_jacobian(self.h, _ptr(x), _ptr(y), int(prec), _stream(stream)),
+                  "mf_apply_jacobian")
+
+    def diagonal(self, out, prec=MF_FP64, stream=None):
+        self._chk(self.lib.mf_diagonal(self.h, _ptr(out), int(prec), _stream(stream)), "mf_diagonal")
+
+    def solve_step(self, up, opts=None, stream=None):
+        rep = MfSolveReport()
+        o = opts if opts is not None else solver_defaults()
+        st = self.lib.mf_solve_step(self.h, _ptr(up), C.byref(o), C.byref(rep), _stream(stream))
+        return st, rep

@@ -1,0 +1,81 @@
+"""ctypes binding of libmf.so (argument marshalling only; all compute runs in the CUDA library)."""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmf.so")
+
+MF_OK, MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_OOM, MF_ERR_STATE, MF_ERR_NAN, MF_ERR_NOT_CONVERGED, \
+    MF_ERR_BREAKDOWN, MF_ERR_ITER_LIMIT = range(9)
+STATUS_NAMES = ["MF_OK", "MF_ERR_ARG", "MF_ERR_CUDA", "MF_ERR_OOM", "MF_ERR_STATE", "MF_ERR_NAN",
+                "MF_ERR_NOT_CONVERGED", "MF_ERR_BREAKDOWN", "MF_ERR_ITER_LIMIT"]
+MF_FP64, MF_FP32 = 0, 1
+MF_PC_JACOBI, MF_PC_CHEBYSHEV = 0, 1
+
+# every symbol include/mf.h declares
+EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_create", "mf_destroy", "mf_last_error", "mf_sizes",
+           "mf_set_angle", "mf_node_coords", "mf_dirichlet", "mf_set_history", "mf_set_linearization",
+           "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step"]
+
+
+class MfOptions(C.Structure):
+    _fields_ = [("penalty_F", C.c_double), ("reserved", C.c_int * 8)]
+
+
+class MfSolverOpts(C.Structure):
+    _fields_ = [("newton_rtol", C.c_double), ("newton_atol", C.c_double), ("max_newton", C.c_int),
+                ("lin_rtol", C.c_double), ("restart", C.c_int), ("max_lin_iters", C.c_int),
+                ("pc", C.c_int), ("pc_precision", C.c_int), ("cheb_degree", C.c_int),
+                ("cheb_lo", C.c_double), ("theta", C.c_double)]
+
+
+class MfSolveReport(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("lin_iters_total", C.c_int), ("lin_iters", C.c_int * 64),
+                ("res_norm", C.c_double * 65), ("lambda_max", C.c_double), ("seconds", C.c_double),
+                ("status", C.c_int)]
+
+
+class MfError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load():
+    """Load libmf.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise MfError(f"{LIB_PATH} not built: run paper_2608_27423_b300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, dbl, i32 = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    lib.mf_mesh_from_arrays.argtypes = [i32, i32, i64, vp, vp, vp, i64, vp, vp, dbl, i32, i32, dbl, dbl, vp, vp,
+                                        C.POINTER(vp)]
+    lib.mf_mesh_free.argtypes = [vp]
+    lib.mf_mesh_free.restype = None
+    lib.mf_create.argtypes = [vp, i32, dbl, dbl, dbl, i32, vp, C.POINTER(vp)]
+    lib.mf_destroy.argtypes = [vp]
+    lib.mf_last_error.argtypes = [vp]
+    lib.mf_last_error.restype = C.c_char_p
+    lib.mf_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    lib.mf_set_angle.argtypes = [vp, dbl, vp]
+    lib.mf_node_coords.argtypes = [vp, vp, vp]
+    lib.mf_dirichlet.argtypes = [vp, vp, vp]
+    lib.mf_set_history.argtypes = [vp, vp, vp, vp]
+    lib.mf_set_linearization.argtypes = [vp, vp, dbl, vp]
+    lib.mf_residual.argtypes = [vp, vp, vp, vp]
+    lib.mf_apply_jacobian.argtypes = [vp, vp, vp, i32, vp]
+    lib.mf_diagonal.argtypes = [vp, vp, i32, vp]
+    lib.mf_solver_defaults.argtypes = [C.POINTER(MfSolverOpts)]
+    lib.mf_solver_defaults.restype = None
+    lib.mf_solve_step.argtypes = [vp, vp, C.POINTER(MfSolverOpts), C.POINTER(MfSolveReport), vp]
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        if name not in ("mf_mesh_free", "mf_last_error", "mf_solver_defaults"):
+            f.restype = C.c_int
+    _lib = lib
+    return lib

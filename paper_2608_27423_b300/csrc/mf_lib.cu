@@ -1,0 +1,421 @@
+// C ABI of the rotor-stator operator library: context set-up, operator calls
+// and the Newton / FGMRES solve.  See include/mf.h for the contract.
+#include <cuda_runtime.h>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/mf.h"
+#include "mf_cell.cuh"
+#include "mf_mortar.cuh"
+#include "mf_small.cuh"
+
+using namespace mf;
+
+struct mf_mesh {
+  int d, k;
+  int64_t nn, nc;
+  std::vector<double> x0;
+  std::vector<uint8_t> node_side, wall, cell_side;
+  std::vector<int32_t> cells;
+  double R, H, phi0;
+  int n_R, n_z;
+  std::vector<int32_t> ifr, ifs;
+};
+
+struct Workspace {
+  int m = 0;                 // restart length allocated
+  double* V = nullptr;       // [m+1][n]
+  double* Z = nullptr;       // [m][n]
+  double* w = nullptr;       // [n]
+  double* r = nullptr;       // [n] residual / rhs
+  double* dx = nullptr;      // [n]
+  double* hcol = nullptr;    // [m+2] device column of H (and scratch)
+  double* part = nullptr;    // [m+2][nb] partial sums
+  double* diag64 = nullptr;  // [n]
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  float* f_v = nullptr;      // FP32 Chebyshev vectors
+  float* f_x = nullptr;
+  float* f_r = nullptr;
+  float* f_d = nullptr;
+  float* f_t = nullptr;
+  double* c_x = nullptr;     // FP64 Chebyshev vectors
+  double* c_r = nullptr;
+  double* c_d = nullptr;
+  double* c_t = nullptr;
+  double* pinned = nullptr;  // host [m+2]
+};
+
+struct mf_ctx {
+  int d = 0, k = 0;
+  int64_t nn = 0, nc = 0, ndof = 0;
+  double nu = 0, omega = 0, dt = 0, a0dt = 0, inv_dt2 = 0, alpha[3] = {0, 0, 0}, F = 1.0;
+  int bdf = 1;
+  double R = 0, H = 1, phi0 = 0, theta = 0;
+  int n_R = 0, n_z = 1;
+  int64_t nm = 0, nwall = 0, nif = 0;
+  bool have_lin = false;
+  int ncache = 0;
+  int nb = 0;  // blocks for reductions
+  // device
+  double *x0 = nullptr, *x = nullptr;
+  uint8_t *node_side = nullptr, *cell_side = nullptr;
+  int32_t *cells = nullptr, *wall = nullptr, *ifr = nullptr, *ifs = nullptr;
+  double *tau_r = nullptr, *tau_s = nullptr;
+  int32_t* mc_cell = nullptr;
+  double *mc_tau = nullptr, *mc_xi = nullptr, *mc_ang = nullptr, *mc_w = nullptr;
+  double *ht = nullptr, *g = nullptr;
+  double* cache64 = nullptr;
+  float* cache32 = nullptr;
+  Workspace ws;
+  std::string err;
+};
+
+static bool g_tabs_ready[64] = {false};
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      if (h) h->err = std::string(#call) + ": " + cudaGetErrorString(e_);             \
+      return e_ == cudaErrorMemoryAllocation ? MF_ERR_OOM : MF_ERR_CUDA;               \
+    }                                                                                  \
+  } while (0)
+
+static inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static mf_status upload_tables(mf_ctx* h) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 64 && g_tabs_ready[dev]) return MF_OK;
+  MfTab<double> t64[MF_KMAX + 1];
+  MfTab<float> t32[MF_KMAX + 1];
+  std::memset(t64, 0, sizeof(t64));
+  std::memset(t32, 0, sizeof(t32));
+  for (int k = 1; k <= MF_KMAX; ++k) {
+    mfhost::build_tab(k, t64[k]);
+    mfhost::cast_tab(t64[k], t32[k]);
+  }
+  CK(cudaMemcpyToSymbol(c_tab64, t64, sizeof(t64)));
+  CK(cudaMemcpyToSymbol(c_tab32, t32, sizeof(t32)));
+  if (dev < 64) g_tabs_ready[dev] = true;
+  return MF_OK;
+}
+
+// ------------------------------------------------------------------ dispatch
+#define MF_DISPATCH(D_, K_, CALL)                                              \
+  switch ((D_) * 10 + (K_)) {                                                  \
+    case 21: { constexpr int D = 2, K = 1; CALL; } break;                      \
+    case 22: { constexpr int D = 2, K = 2; CALL; } break;                      \
+    case 23: { constexpr int D = 2, K = 3; CALL; } break;                      \
+    case 24: { constexpr int D = 2, K = 4; CALL; } break;                      \
+    case 25: { constexpr int D = 2, K = 5; CALL; } break;                      \
+    case 31: { constexpr int D = 3, K = 1; CALL; } break;                      \
+    case 32: { constexpr int D = 3, K = 2; CALL; } break;                      \
+    case 33: { constexpr int D = 3, K = 3; CALL; } break;                      \
+    case 34: { constexpr int D = 3, K = 4; CALL; } break;                      \
+    case 35: { constexpr int D = 3, K = 5; CALL; } break;                      \
+    default: break;                                                            \
+  }
+
+template <int D, int K>
+static void launch_state(mf_ctx* h, int mode, const double* up, double* dst, cudaStream_t st) {
+  StateArgs A;
+  A.cells = h->cells; A.nc = h->nc; A.x = h->x; A.cell_side = h->cell_side; A.up = up; A.ht = h->ht;
+  A.cache = h->cache64; A.dst = dst; A.nu = h->nu; A.omega = h->omega; A.a0dt = h->a0dt; A.inv_dt2 = h->inv_dt2;
+  using C = CellCfg<D, K>;
+  const unsigned g = nblk(h->nc, C::CPB);
+  if (mode == 0) k_cell_state<D, K, 0><<<g, C::THREADS, 0, st>>>(A);
+  else k_cell_state<D, K, 1><<<g, C::THREADS, 0, st>>>(A);
+}
+
+template <int D, int K, typename T>
+static void launch_jac(mf_ctx* h, const T* cache, const T* x, T* y, cudaStream_t st) {
+  using C = CellCfg<D, K>;
+  const unsigned g = nblk(h->nc, C::CPB);
+  k_cell_jac<D, K, T><<<g, C::THREADS, 0, st>>>(h->cells, h->nc, cache, x, y, (T)h->nu, (T)h->a0dt);
+}
+
+template <int D, int K, typename T>
+static void launch_mortar(mf_ctx* h, int mode, const T* src, T* dst, int zero_wall, cudaStream_t st) {
+  MortarArgs<T> A;
+  A.cells = h->cells; A.x = h->x; A.mc_cell = h->mc_cell; A.mc_tau = h->mc_tau; A.mc_xi = h->mc_xi;
+  A.mc_ang = h->mc_ang; A.mc_w = h->mc_w; A.nm = h->nm; A.src = src; A.dst = dst; A.nu = (T)h->nu;
+  A.dz = h->H / h->n_z; A.zero_wall = zero_wall;
+  using C = MortarCfg<D, K>;
+  const unsigned g = nblk(h->nm, C::MPB);
+  if (mode == 0) k_mortar<D, K, T, 0><<<g, C::THREADS, 0, st>>>(A);
+  else k_mortar<D, K, T, 1><<<g, C::THREADS, 0, st>>>(A);
+}
+
+template <int D, int K, typename T>
+static void launch_cell_diag(mf_ctx* h, const T* cache, T* diag, cudaStream_t st) {
+  using C = CellCfg<D, K>;
+  k_cell_diag<D, K, T><<<nblk(h->nc, C::CPB), C::THREADS, 0, st>>>(h->cells, h->nc, cache, diag, (T)h->nu, (T)h->a0dt);
+}
+
+template <int D, int K>
+static void launch_penalty(mf_ctx* h, cudaStream_t st) {
+  const int64_t nif = (int64_t)h->n_z * h->n_R;
+  k_penalty<D, K><<<nblk(nif, 64), 64, 0, st>>>(h->cells, h->x, h->ifr, nif, 0, h->F, h->tau_r);
+  k_penalty<D, K><<<nblk(nif, 64), 64, 0, st>>>(h->cells, h->x, h->ifs, nif, 1, h->F, h->tau_s);
+}
+
+template <int K>
+static void launch_map(mf_ctx* h, cudaStream_t st) {
+  MortarMap A;
+  A.mc_cell = h->mc_cell; A.mc_tau = h->mc_tau; A.mc_xi = h->mc_xi; A.mc_ang = h->mc_ang; A.mc_w = h->mc_w;
+  A.ifr = h->ifr; A.ifs = h->ifs; A.tau_r = h->tau_r; A.tau_s = h->tau_s; A.n_R = h->n_R; A.n_z = h->n_z;
+  A.R = h->R; A.phi0 = h->phi0; A.theta = h->theta;
+  k_mortar_map<K><<<nblk(h->nm, 128), 128, 0, st>>>(A);
+}
+
+// ------------------------------------------------------------------ mesh
+extern "C" mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const double* x0, const uint8_t* node_side,
+                                         const uint8_t* wall, int64_t n_cells, const int32_t* cells,
+                                         const uint8_t* cell_side, double R, int n_R, int n_z, double H, double phi0,
+                                         const int32_t* iface_rotor, const int32_t* iface_stator, mf_mesh** out) {
+  if (!out || !x0 || !node_side || !wall || !cells || !cell_side || !iface_rotor || !iface_stator) return MF_ERR_ARG;
+  if ((d != 2 && d != 3) || k < 1 || k > MF_KMAX || n_nodes <= 0 || n_cells <= 0 || n_R < 1 || n_z < 1 ||
+      !(R > 0) || (d == 3 && !(H > 0)))
+    return MF_ERR_ARG;
+  if (n_nodes >= (int64_t)1 << 31) return MF_ERR_ARG;
+  if (d == 2) n_z = 1;
+  const int npc = ipow(k + 1, d);
+  mf_mesh* m = new mf_mesh();
+  m->d = d; m->k = k; m->nn = n_nodes; m->nc = n_cells; m->R = R; m->H = (d == 2 ? 1.0 : H); m->phi0 = phi0;
+  m->n_R = n_R; m->n_z = n_z;
+  m->x0.assign(x0, x0 + n_nodes * d);
+  m->node_side.assign(node_side, node_side + n_nodes);
+  m->wall.assign(wall, wall + n_nodes);
+  m->cells.assign(cells, cells + n_cells * npc);
+  m->cell_side.assign(cell_side, cell_side + n_cells);
+  m->ifr.assign(iface_rotor, iface_rotor + (int64_t)n_z * n_R);
+  m->ifs.assign(iface_stator, iface_stator + (int64_t)n_z * n_R);
+  for (int32_t c : m->cells)
+    if (c < 0 || c >= n_nodes) { delete m; return MF_ERR_ARG; }
+  for (int64_t i = 0; i < (int64_t)n_z * n_R; ++i)
+    if (m->ifr[i] < 0 || m->ifr[i] >= n_cells || m->ifs[i] < 0 || m->ifs[i] >= n_cells) { delete m; return MF_ERR_ARG; }
+  *out = m;
+  return MF_OK;
+}
+
+extern "C" void mf_mesh_free(mf_mesh* m) { delete m; }
+
+// ------------------------------------------------------------------ create
+static void free_ws(Workspace& w) {
+  void* ptrs[] = {w.V, w.Z, w.w, w.r, w.dx, w.hcol, w.part, w.diag64, w.dinv64, w.dinv32, w.f_v, w.f_x, w.f_r,
+                  w.f_d, w.f_t, w.c_x, w.c_r, w.c_d, w.c_t};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  if (w.pinned) cudaFreeHost(w.pinned);
+  w = Workspace();
+}
+
+extern "C" mf_status mf_destroy(mf_handle h) {
+  if (!h) return MF_ERR_ARG;
+  void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
+                  h->mc_cell, h->mc_tau, h->mc_xi, h->mc_ang, h->mc_w, h->ht, h->g, h->cache64, h->cache32};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  free_ws(h->ws);
+  delete h;
+  return MF_OK;
+}
+
+extern "C" const char* mf_last_error(mf_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+static mf_status apply_angle(mf_ctx* h, double theta, cudaStream_t st) {
+  h->theta = theta;
+  const double ct = cos(theta), sn = sin(theta);
+  if (h->d == 2) k_rotate<2><<<nblk(h->nn, 256), 256, 0, st>>>(h->x0, h->node_side, h->x, h->nn, ct, sn);
+  else k_rotate<3><<<nblk(h->nn, 256), 256, 0, st>>>(h->x0, h->node_side, h->x, h->nn, ct, sn);
+  switch (h->k) {
+    case 1: launch_map<1>(h, st); break;
+    case 2: launch_map<2>(h, st); break;
+    case 3: launch_map<3>(h, st); break;
+    case 4: launch_map<4>(h, st); break;
+    case 5: launch_map<5>(h, st); break;
+  }
+  CK(cudaGetLastError());
+  return MF_OK;
+}
+
+extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega, double dt, int bdf,
+                               const mf_options* opt, mf_handle* out) {
+  if (!m || !out) return MF_ERR_ARG;
+  if (k != m->k || !(nu >= 0) || !std::isfinite(omega) || !(dt >= 0) || (bdf != 1 && bdf != 2)) return MF_ERR_ARG;
+  mf_ctx* h = new mf_ctx();
+  h->d = m->d; h->k = k; h->nn = m->nn; h->nc = m->nc; h->ndof = m->nn * (m->d + 1);
+  h->nu = nu; h->omega = omega; h->dt = dt; h->bdf = bdf;
+  h->F = (opt && opt->penalty_F > 0) ? opt->penalty_F : 1.0;
+  const double al1[3] = {1.0, -1.0, 0.0}, al2[3] = {1.5, -2.0, 0.5};
+  for (int i = 0; i < 3; ++i) h->alpha[i] = bdf == 1 ? al1[i] : al2[i];
+  h->a0dt = dt > 0 ? h->alpha[0] / dt : 0.0;
+  h->inv_dt2 = dt > 0 ? 1.0 / (dt * dt) : 0.0;
+  h->R = m->R; h->H = m->H; h->phi0 = m->phi0; h->n_R = m->n_R; h->n_z = m->n_z;
+  h->nm = (int64_t)m->n_z * m->n_R * 2;
+  h->nif = (int64_t)m->n_z * m->n_R;
+  h->ncache = (m->d == 2) ? Cache<2>::NF : Cache<3>::NF;
+  h->nb = 148 * 4;
+  mf_status s = upload_tables(h);
+  if (s != MF_OK) { mf_destroy(h); return s; }
+  const int npc = ipow(k + 1, m->d);
+  // cell table with wall nodes encoded as ~id
+  std::vector<int32_t> cells(m->cells);
+  for (auto& c : cells) if (m->wall[c]) c = ~c;
+  std::vector<int32_t> wl;
+  for (int64_t i = 0; i < m->nn; ++i) if (m->wall[i]) wl.push_back((int32_t)i);
+  h->nwall = (int64_t)wl.size();
+  const size_t nn = m->nn, nc = m->nc, d = m->d;
+#define ALLOC(p, cnt) CK(cudaMalloc((void**)&(p), sizeof(*(p)) * std::max<size_t>(1, (size_t)(cnt))))
+  auto fail = [&](mf_status st) { std::string e = h->err; mf_destroy(h); (void)e; return st; };
+  do {
+#define ALLOC2(p, cnt)                                                                          \
+  if (cudaMalloc((void**)&(p), sizeof(*(p)) * std::max<size_t>(1, (size_t)(cnt))) != cudaSuccess) \
+    return fail(MF_ERR_OOM);
+    ALLOC2(h->x0, nn * d); ALLOC2(h->x, nn * d); ALLOC2(h->node_side, nn); ALLOC2(h->cell_side, nc);
+    ALLOC2(h->cells, nc * npc); ALLOC2(h->wall, wl.size()); ALLOC2(h->ifr, h->nif); ALLOC2(h->ifs, h->nif);
+    ALLOC2(h->tau_r, h->nif); ALLOC2(h->tau_s, h->nif);
+    ALLOC2(h->mc_cell, h->nm * 2); ALLOC2(h->mc_tau, h->nm); ALLOC2(h->mc_xi, h->nm * 2 * (k + 1));
+    ALLOC2(h->mc_ang, h->nm * (k + 1)); ALLOC2(h->mc_w, h->nm * (k + 1));
+    ALLOC2(h->ht, nn * d); ALLOC2(h->cache64, (size_t)h->ncache * nc * npc); ALLOC2(h->cache32, (size_t)h->ncache * nc * npc);
+  } while (0);
+#undef ALLOC2
+  if (cudaMemcpy(h->x0, m->x0.data(), nn * d * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->node_side, m->node_side.data(), nn, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->cell_side, m->cell_side.data(), nc, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->cells, cells.data(), nc * npc * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (wl.size() && cudaMemcpy(h->wall, wl.data(), wl.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(h->ifr, m->ifr.data(), h->nif * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->ifs, m->ifs.data(), h->nif * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(h->ht, 0, nn * d * 8) != cudaSuccess)
+    return fail(MF_ERR_CUDA);
+  // geometry at theta = 0, penalties (rotation-invariant), mortar cells
+  if (h->d == 2) k_rotate<2><<<nblk(h->nn, 256), 256>>>(h->x0, h->node_side, h->x, h->nn, 1.0, 0.0);
+  else k_rotate<3><<<nblk(h->nn, 256), 256>>>(h->x0, h->node_side, h->x, h->nn, 1.0, 0.0);
+  MF_DISPATCH(h->d, h->k, (launch_penalty<D, K>(h, 0)));
+  if (apply_angle(h, 0.0, 0) != MF_OK) return fail(MF_ERR_CUDA);
+  if (cudaDeviceSynchronize() != cudaSuccess) { h->err = cudaGetErrorString(cudaGetLastError()); return fail(MF_ERR_CUDA); }
+  *out = h;
+  return MF_OK;
+#undef ALLOC
+}
+
+extern "C" mf_status mf_sizes(mf_handle h, int64_t* n_nodes, int64_t* n_dofs, int64_t* n_cells, int64_t* n_mortar) {
+  if (!h) return MF_ERR_ARG;
+  if (n_nodes) *n_nodes = h->nn;
+  if (n_dofs) *n_dofs = h->ndof;
+  if (n_cells) *n_cells = h->nc;
+  if (n_mortar) *n_mortar = h->nm;
+  return MF_OK;
+}
+
+extern "C" mf_status mf_set_angle(mf_handle h, double theta, void* stream) {
+  if (!h) return MF_ERR_ARG;
+  if (!std::isfinite(theta)) { h->err = "theta must be finite"; return MF_ERR_ARG; }
+  h->have_lin = false;
+  return apply_angle(h, theta, S(stream));
+}
+
+extern "C" mf_status mf_node_coords(mf_handle h, double* xyz, void* stream) {
+  if (!h || !xyz) return MF_ERR_ARG;
+  CK(cudaMemcpyAsync(xyz, h->x, h->nn * h->d * 8, cudaMemcpyDeviceToDevice, S(stream)));
+  return MF_OK;
+}
+
+extern "C" mf_status mf_dirichlet(mf_handle h, const double* g, void* stream) {
+  if (!h) return MF_ERR_ARG;
+  if (!g) { if (h->g) { cudaFree(h->g); h->g = nullptr; } return MF_OK; }
+  if (!h->g) CK(cudaMalloc((void**)&h->g, h->nn * h->d * 8));
+  CK(cudaMemcpyAsync(h->g, g, h->nn * h->d * 8, cudaMemcpyDeviceToDevice, S(stream)));
+  return MF_OK;
+}
+
+extern "C" mf_status mf_set_history(mf_handle h, const double* u_n, const double* u_nm1, void* stream) {
+  if (!h || !u_n || (h->bdf == 2 && !u_nm1)) return MF_ERR_ARG;
+  if (h->dt <= 0) { CK(cudaMemsetAsync(h->ht, 0, h->nn * h->d * 8, S(stream))); return MF_OK; }
+  const int64_t n = h->nn * h->d;
+  k_history<<<nblk(n, 256), 256, 0, S(stream)>>>(u_n, h->bdf == 2 ? u_nm1 : nullptr, h->ht, n, h->alpha[1] / h->dt,
+                                                 h->alpha[2] / h->dt);
+  CK(cudaGetLastError());
+  return MF_OK;
+}
+
+extern "C" mf_status mf_set_linearization(mf_handle h, const double* up_star, double theta, void* stream) {
+  if (!h || !up_star) return MF_ERR_ARG;
+  if (!std::isfinite(theta)) { h->err = "theta must be finite"; return MF_ERR_ARG; }
+  cudaStream_t st = S(stream);
+  mf_status s = apply_angle(h, theta, st);
+  if (s != MF_OK) return s;
+  MF_DISPATCH(h->d, h->k, (launch_state<D, K>(h, 0, up_star, nullptr, st)));
+  const int64_t ncv = (int64_t)h->ncache * h->nc * ipow(h->k + 1, h->d);
+  k_cast<double, float><<<nblk(ncv, 256), 256, 0, st>>>(h->cache64, h->cache32, ncv);
+  CK(cudaGetLastError());
+  h->have_lin = true;
+  return MF_OK;
+}
+
+extern "C" mf_status mf_residual(mf_handle h, const double* up, double* r, void* stream) {
+  if (!h || !up || !r) return MF_ERR_ARG;
+  cudaStream_t st = S(stream);
+  CK(cudaMemsetAsync(r, 0, h->ndof * 8, st));
+  MF_DISPATCH(h->d, h->k, (launch_state<D, K>(h, 1, up, r, st)));
+  MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, double>(h, 0, up, r, 0, st)));
+  if (h->nwall) {
+    if (h->d == 2) k_dirichlet_res<2><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, up, h->g, r);
+    else k_dirichlet_res<3><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, up, h->g, r);
+  }
+  CK(cudaGetLastError());
+  return MF_OK;
+}
+
+template <typename T>
+static mf_status apply_t(mf_ctx* h, const T* x, T* y, cudaStream_t st) {
+  const T* cache = std::is_same<T, double>::value ? (const T*)h->cache64 : (const T*)h->cache32;
+  CK(cudaMemsetAsync(y, 0, h->ndof * sizeof(T), st));
+  MF_DISPATCH(h->d, h->k, (launch_jac<D, K, T>(h, cache, x, y, st)));
+  MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 0, x, y, 1, st)));
+  if (h->nwall) {
+    if (h->d == 2) k_dirichlet_copy<2, T><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, x, y);
+    else k_dirichlet_copy<3, T><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, x, y);
+  }
+  CK(cudaGetLastError());
+  return MF_OK;
+}
+
+extern "C" mf_status mf_apply_jacobian(mf_handle h, const void* x, void* y, mf_precision prec, void* stream) {
+  if (!h || !x || !y || x == y) return MF_ERR_ARG;
+  if (!h->have_lin) { h->err = "mf_apply_jacobian before mf_set_linearization"; return MF_ERR_STATE; }
+  if (prec == MF_FP64) return apply_t<double>(h, (const double*)x, (double*)y, S(stream));
+  if (prec == MF_FP32) return apply_t<float>(h, (const float*)x, (float*)y, S(stream));
+  return MF_ERR_ARG;
+}
+
+template <typename T>
+static mf_status diag_t(mf_ctx* h, T* dg, cudaStream_t st) {
+  const T* cache = std::is_same<T, double>::value ? (const T*)h->cache64 : (const T*)h->cache32;
+  CK(cudaMemsetAsync(dg, 0, h->ndof * sizeof(T), st));
+  MF_DISPATCH(h->d, h->k, (launch_cell_diag<D, K, T>(h, cache, dg, st)));
+  MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 1, (const T*)nullptr, dg, 1, st)));
+  if (h->nwall) {
+    if (h->d == 2) k_dirichlet_one<2, T><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, dg);
+    else k_dirichlet_one<3, T><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, dg);
+  }
+  CK(cudaGetLastError());
+  return MF_OK;
+}
+
+extern "C" mf_status mf_diagonal(mf_handle h, void* diag_out, mf_precision prec, void* stream) {
+  if (!h || !diag_out) return MF_ERR_ARG;
+  if (!h->have_lin) { h->err = "mf_diagonal before mf_set_linearization"; return MF_ERR_STATE; }
+  if (prec == MF_FP64) return diag_t<double>(h, (double*)diag_out, S(stream));
+  if (prec == MF_FP32) return diag_t<float>(h, (float*)diag_out, S(stream));
+  return MF_ERR_ARG;
+}
+
+#include "mf_solve.inc"

@@ -1,0 +1,438 @@
+// Mortar interface kernels: rotor rotation (Section 3.1), mortar-cell mapping
+// (Section 3.2), Hillewaert penalty (Eq. EqPenalty) and the Nitsche/SIPG face
+// terms of Eq. Eq-NSweakWmortar (pressure central flux, SIPG consistency,
+// symmetry and penalty terms, strong-DG mass term).
+#pragma once
+#include "mf_cell.cuh"
+
+namespace mf {
+
+// 1D Lagrange values/derivatives on the Gauss-Lobatto nodes at an arbitrary t.
+template <int N, typename T>
+__device__ __forceinline__ void lagrange_at(const MfTab<T>& tb, T t, T* L, T* dL) {
+#pragma unroll
+  for (int b = 0; b < N; ++b) {
+    T v = T(1), d = T(0);
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      if (c == b) continue;
+      d = d * (t - tb.gll[c]) + v;     // product rule, accumulated left to right
+      v = v * (t - tb.gll[c]);
+    }
+    L[b] = v * tb.bw[b];
+    dL[b] = d * tb.bw[b];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x = R(theta) x0 for rotor nodes (2D rotation matrix; 3D
+// R = cos I + sin W + (1 - cos) r (x) r with axis r = e_z), x = x0 otherwise.
+template <int D>
+__global__ void k_rotate(const double* __restrict__ x0, const uint8_t* __restrict__ side, double* __restrict__ x,
+                         int64_t nn, double ct, double st) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  double p[3] = {x0[i * D], x0[i * D + 1], D == 3 ? x0[i * D + 2] : 0.0};
+  if (side[i] == 0) {
+    const double r[3] = {0.0, 0.0, 1.0};
+    double Rm[3][3];
+    const double W[3][3] = {{0.0, -r[2], r[1]}, {r[2], 0.0, -r[0]}, {-r[1], r[0], 0.0}};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Rm[a][b] = (a == b ? ct : 0.0) + st * W[a][b] + (1.0 - ct) * r[a] * r[b];
+    double q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) q[a] = Rm[a][0] * p[0] + Rm[a][1] * p[1] + Rm[a][2] * p[2];
+    p[0] = q[0]; p[1] = q[1]; p[2] = q[2];
+  }
+#pragma unroll
+  for (int m = 0; m < D; ++m) x[i * D + m] = p[m];
+}
+
+// ---------------------------------------------------------------------------
+// Mortar cells at rotor angle theta.  With D = 2 pi / n_R, theta = s D + th
+// (0 <= th < D), stator cell js of layer lz is cut by one rotor vertex into
+//   half 0: angles [js D, js D + th], covered by rotor cell js - s - 1,
+//   half 1: angles [js D + th, (js+1) D], covered by rotor cell js - s,
+// (angles relative to phi0; a half of zero length gets zero weights).
+// Gauss rule mapped into each half: weight w_g R L, point on the exact circle,
+// each side's face coordinate linear in the angle.
+struct MortarMap {
+  int32_t* mc_cell;   // [M][2] rotor, stator cell
+  double* mc_tau;     // [M] face penalty max(tau_rotor, tau_stator)
+  double* mc_xi;      // [M][2][N] face coordinate on each side
+  double* mc_ang;     // [M][N] absolute angle of the point
+  double* mc_w;       // [M][N] angular weight w_g R L
+  const int32_t* ifr; // [n_z][n_R]
+  const int32_t* ifs;
+  const double* tau_r; // [n_z][n_R] tau_k of rotor interface cells
+  const double* tau_s;
+  int n_R, n_z;
+  double R, phi0, theta;
+};
+
+template <int K>
+__global__ void k_mortar_map(MortarMap A) {
+  constexpr int N = K + 1;
+  const int64_t M = (int64_t)A.n_z * A.n_R * 2;
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int h = (int)(m & 1);
+  const int js = (int)((m >> 1) % A.n_R);
+  const int lz = (int)((m >> 1) / A.n_R);
+  const double Dl = 2.0 * M_PI / A.n_R;
+  const double sf = floor(A.theta / Dl);
+  double th = A.theta - sf * Dl;
+  if (th < 0.0) th = 0.0;
+  if (th > Dl) th = Dl;
+  long long si = (long long)sf % A.n_R;
+  if (si < 0) si += A.n_R;
+  int jr = (int)(((long long)js - si - (h == 0 ? 1 : 0)) % A.n_R);
+  if (jr < 0) jr += A.n_R;
+  const double L = (h == 0) ? th : Dl - th;
+  const double start = js * Dl + (h == 0 ? 0.0 : th);
+  const MfTab<double>& tb = c_tab64[K];
+  A.mc_cell[2 * m] = A.ifr[(int64_t)lz * A.n_R + jr];
+  A.mc_cell[2 * m + 1] = A.ifs[(int64_t)lz * A.n_R + js];
+  A.mc_tau[m] = fmax(A.tau_r[(int64_t)lz * A.n_R + jr], A.tau_s[(int64_t)lz * A.n_R + js]);
+#pragma unroll
+  for (int g = 0; g < N; ++g) {
+    const double sg = tb.s[g];
+    // stator: (phi - js D)/D ; rotor: (phi - start of rotor cell)/D
+    const double xs = (h == 0) ? sg * th / Dl : (th + sg * (Dl - th)) / Dl;
+    const double xr = (h == 0) ? 1.0 - (1.0 - sg) * th / Dl : sg * (Dl - th) / Dl;
+    A.mc_xi[(m * 2 + 0) * N + g] = xr;
+    A.mc_xi[(m * 2 + 1) * N + g] = xs;
+    A.mc_ang[m * N + g] = A.phi0 + start + sg * L;
+    A.mc_w[m * N + g] = tb.w[g] * A.R * L;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Penalty tau_k = F (k+1)^2 (A(other faces)/2 + A(interface face)) / V of each
+// interface cell (Eq. EqPenalty; all non-interface faces halved).  Face areas
+// and the volume by the (k+1)-point Gauss rule on the isoparametric map.
+// Interface face: xi_0 = 1 (rotor, side 0) or xi_0 = 0 (stator, side 1).
+template <int D, int K>
+__global__ void k_penalty(const int32_t* __restrict__ cells, const double* __restrict__ x,
+                          const int32_t* __restrict__ iface, int64_t ncell_if, int side, double F,
+                          double* __restrict__ tau_out) {
+  constexpr int N = K + 1, NPC = ipow(N, D);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncell_if) return;
+  const MfTab<double>& tb = c_tab64[K];
+  const int64_t cell = iface[i];
+  double X[NPC][D];
+  for (int b = 0; b < NPC; ++b) {
+    int id = cells[cell * NPC + b];
+    id = id < 0 ? ~id : id;
+    for (int m = 0; m < D; ++m) X[b][m] = x[(int64_t)id * D + m];
+  }
+  double area_if = 0.0, area_other = 0.0, vol = 0.0;
+  double L0[N], dL0[N], L1[N], dL1[N], L2[N], dL2[N];
+  // volume
+  const int nq = ipow(N, D);
+  for (int q = 0; q < nq; ++q) {
+    int qi[3] = {q % N, (q / N) % N, q / (N * N)};
+    double J[3][3] = {{0}};
+    for (int b = 0; b < NPC; ++b) {
+      int bi[3] = {b % N, (b / N) % N, b / (N * N)};
+      double dphi[3];
+      for (int r = 0; r < D; ++r) {
+        double p = 1.0;
+        for (int u = 0; u < D; ++u) p *= (u == r) ? tb.Dn[qi[u]][bi[u]] : tb.B[qi[u]][bi[u]];
+        dphi[r] = p;
+      }
+      for (int m = 0; m < D; ++m)
+        for (int r = 0; r < D; ++r) J[m][r] += X[b][m] * dphi[r];
+    }
+    double det = (D == 2) ? J[0][0] * J[1][1] - J[0][1] * J[1][0]
+                          : J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    double wq = 1.0;
+    for (int u = 0; u < D; ++u) wq *= tb.w[qi[u]];
+    vol += det * wq;
+  }
+  // faces xi_r = sd
+  for (int r = 0; r < D; ++r)
+    for (int sd = 0; sd < 2; ++sd) {
+      double fa = 0.0;
+      const int nfq = ipow(N, D - 1);
+      for (int fq = 0; fq < nfq; ++fq) {
+        // tangential directions t0 < t1 (3D) or t0 (2D)
+        int tdir[2], k2 = 0;
+        for (int u = 0; u < D; ++u) if (u != r) tdir[k2++] = u;
+        double xi[3];
+        xi[r] = (double)sd;
+        xi[tdir[0]] = tb.s[fq % N];
+        if (D == 3) xi[tdir[1]] = tb.s[fq / N];
+        double wf = tb.w[fq % N] * (D == 3 ? tb.w[fq / N] : 1.0);
+        lagrange_at<N, double>(tb, xi[0], L0, dL0);
+        lagrange_at<N, double>(tb, xi[1], L1, dL1);
+        if (D == 3) lagrange_at<N, double>(tb, xi[2], L2, dL2);
+        double J[3][3] = {{0}};
+        for (int b = 0; b < NPC; ++b) {
+          int b0 = b % N, b1 = (b / N) % N, b2 = b / (N * N);
+          double l2 = D == 3 ? L2[b2] : 1.0, d2 = D == 3 ? dL2[b2] : 0.0;
+          double dphi[3] = {dL0[b0] * L1[b1] * l2, L0[b0] * dL1[b1] * l2, L0[b0] * L1[b1] * d2};
+          for (int m = 0; m < D; ++m)
+            for (int u = 0; u < D; ++u) J[m][u] += X[b][m] * dphi[u];
+        }
+        double da;
+        if (D == 2) {
+          da = sqrt(J[0][tdir[0]] * J[0][tdir[0]] + J[1][tdir[0]] * J[1][tdir[0]]);
+        } else {
+          double t0[3] = {J[0][tdir[0]], J[1][tdir[0]], J[2][tdir[0]]};
+          double t1[3] = {J[0][tdir[1]], J[1][tdir[1]], J[2][tdir[1]]};
+          double c0 = t0[1] * t1[2] - t0[2] * t1[1];
+          double c1 = t0[2] * t1[0] - t0[0] * t1[2];
+          double c2 = t0[0] * t1[1] - t0[1] * t1[0];
+          da = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+        }
+        fa += da * wf;
+      }
+      const int face_if_sd = (side == 0) ? 1 : 0;
+      if (r == 0 && sd == face_if_sd) area_if += fa; else area_other += fa;
+    }
+  tau_out[i] = F * (double)(N * N) * (0.5 * area_other + area_if) / vol;
+}
+
+// ---------------------------------------------------------------------------
+// Face terms.  MODE 0: dst += M src (Jacobian / residual, linear in src);
+// MODE 1: diag += diagonal of the face operator.  Per mortar cell and side s
+// (own = s, other = 1-s; jump = own - other; n_s own outward normal):
+//   -(q, 1/2 [[u]].n) + (v, {p} n) - (grad v : nu/2 [[u]] (x) n)
+//   - (v, nu {grad u} n) + (v, nu tau [[u]])
+template <int D, int K> struct MortarCfg {
+  static constexpr int N = K + 1, NPC = ipow(N, D), NP = ipow(N, D - 1);
+  static constexpr int MPB = (2 * NPC >= 128) ? 1 : (256 / (2 * NPC));
+  static constexpr int THREADS = MPB * 2 * NPC;
+};
+
+template <typename T> struct MortarArgs {
+  const int32_t* cells; const double* x;
+  const int32_t* mc_cell; const double* mc_tau; const double* mc_xi; const double* mc_ang; const double* mc_w;
+  int64_t nm;
+  const T* src; T* dst;
+  T nu; double dz; int zero_wall;
+};
+
+template <int D, int K, typename T, int MODE>
+__global__ void __launch_bounds__(MortarCfg<D, K>::THREADS) k_mortar(MortarArgs<T> A) {
+  using C = MortarCfg<D, K>;
+  constexpr int N = C::N, NPC = C::NPC, NP = C::NP, NF = D + 1, MPB = C::MPB;
+  __shared__ T s_val[MPB][2][NPC][NF];
+  __shared__ T s_X[MPB][2][NPC][D];
+  __shared__ T s_U[MPB][2][NP][NF];
+  __shared__ T s_GU[MPB][2][NP][D][D];
+  __shared__ T s_Ji[MPB][2][NP][D][D];
+  __shared__ T s_L1[MPB][2][N][N];
+  __shared__ T s_dL1[MPB][2][N][N];
+  __shared__ T s_fv[MPB][2][NP][NF];
+  __shared__ T s_Fx[MPB][2][NP][D][D];
+  const MfTab<T>& tb = TabSel<T>::get(K);
+  const int lm = threadIdx.x / (2 * NPC);
+  const int loc = threadIdx.x % (2 * NPC);
+  const int s = loc / NPC, a = loc % NPC;
+  const int64_t mc = (int64_t)blockIdx.x * MPB + lm;
+  const bool active = mc < A.nm;
+  // ---- phase 1: gather the two cells
+  int node = 0;
+  {
+    const int cell = active ? A.mc_cell[2 * mc + s] : 0;
+    if (active) {
+      const int id = A.cells[(int64_t)cell * NPC + a];
+      const bool wall = id < 0;
+      node = wall ? ~id : id;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) s_val[lm][s][a][f] = (MODE == 0) ? A.src[(int64_t)node * NF + f] : T(0);
+      if (MODE == 0 && wall && A.zero_wall) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) s_val[lm][s][a][c] = T(0);
+      }
+#pragma unroll
+      for (int m = 0; m < D; ++m) s_X[lm][s][a][m] = (T)A.x[(int64_t)node * D + m];
+    } else {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) s_val[lm][s][a][f] = T(0);
+      const int ai[3] = {a % N, (a / N) % N, a / (N * N)};
+#pragma unroll
+      for (int m = 0; m < D; ++m) s_X[lm][s][a][m] = (T)ai[m];
+    }
+  }
+  __syncthreads();
+  // ---- phase 2: traces at the points of side s
+  const T xi0 = (s == 0) ? T(1) : T(0);
+  T L0[N], dL0[N];
+  lagrange_at<N, T>(tb, xi0, L0, dL0);
+  if (a < NP) {
+    const int p = a, ia = p % N, iz = (D == 3) ? p / N : 0;
+    const T xi1 = active ? (T)A.mc_xi[(mc * 2 + s) * N + ia] : T(0.5);
+    T L1[N], dL1[N];
+    lagrange_at<N, T>(tb, xi1, L1, dL1);
+    if (iz == 0) {
+#pragma unroll
+      for (int b = 0; b < N; ++b) { s_L1[lm][s][ia][b] = L1[b]; s_dL1[lm][s][ia][b] = dL1[b]; }
+    }
+    T u[NF], du[NF][D], J[D][D];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) { u[f] = T(0);
+#pragma unroll
+      for (int r = 0; r < D; ++r) du[f][r] = T(0); }
+#pragma unroll
+    for (int m = 0; m < D; ++m)
+#pragma unroll
+      for (int r = 0; r < D; ++r) J[m][r] = T(0);
+#pragma unroll
+    for (int b = 0; b < NPC; ++b) {
+      const int b0 = b % N, b1 = (b / N) % N, b2 = b / (N * N);
+      const T l2 = (D == 3) ? tb.B[iz][b2] : T(1);
+      const T d2 = (D == 3) ? tb.Dn[iz][b2] : T(0);
+      const T phi = L0[b0] * L1[b1] * l2;
+      T dphi[3] = {dL0[b0] * L1[b1] * l2, L0[b0] * dL1[b1] * l2, L0[b0] * L1[b1] * d2};
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const T vv = s_val[lm][s][b][f];
+        u[f] = fma(phi, vv, u[f]);
+#pragma unroll
+        for (int r = 0; r < D; ++r) du[f][r] = fma(dphi[r], vv, du[f][r]);
+      }
+#pragma unroll
+      for (int m = 0; m < D; ++m)
+#pragma unroll
+        for (int r = 0; r < D; ++r) J[m][r] = fma(dphi[r], s_X[lm][s][b][m], J[m][r]);
+    }
+    T Ji[D][D];
+    if (D == 2) {
+      const T det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      const T id = T(1) / det;
+      Ji[0][0] = J[1][1] * id; Ji[0][1] = -J[0][1] * id; Ji[1][0] = -J[1][0] * id; Ji[1][1] = J[0][0] * id;
+    } else {
+      T c[3][3];
+      c[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+      c[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+      c[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+      c[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+      c[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+      c[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+      c[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+      c[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+      c[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      const T det = J[0][0] * c[0][0] + J[0][1] * c[0][1] + J[0][2] * c[0][2];
+      const T id = T(1) / det;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) Ji[r][m] = c[m][r] * id;
+    }
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int m = 0; m < D; ++m) s_Ji[lm][s][p][r][m] = Ji[r][m];
+    if (MODE == 0) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) s_U[lm][s][p][f] = u[f];
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          T g = T(0);
+#pragma unroll
+          for (int r = 0; r < D; ++r) g = fma(du[c][r], Ji[r][m], g);
+          s_GU[lm][s][p][c][m] = g;
+        }
+    }
+  }
+  __syncthreads();
+  // ---- phase 3: fluxes of side s at its points
+  const T tau_f = active ? (T)A.mc_tau[mc] : T(0);
+  if (MODE == 0 && a < NP) {
+    const int p = a, ia = p % N, iz = (D == 3) ? p / N : 0;
+    const int o = 1 - s;
+    const double ang = active ? A.mc_ang[mc * N + ia] : 0.0;
+    double wd = active ? A.mc_w[mc * N + ia] : 0.0;
+    if (D == 3) wd *= (double)TabSel<double>::get(K).w[iz] * A.dz;
+    const T w = (T)wd;
+    const T sg = (s == 0) ? T(1) : T(-1);
+    T n[3] = {sg * (T)cos(ang), sg * (T)sin(ang), T(0)};
+    T jump[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) jump[c] = s_U[lm][s][p][c] - s_U[lm][o][p][c];
+    const T pavg = T(0.5) * (s_U[lm][s][p][D] + s_U[lm][o][p][D]);
+    T jn = T(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) jn = fma(jump[c], n[c], jn);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T gn = T(0);
+#pragma unroll
+      for (int m = 0; m < D; ++m) gn = fma(T(0.5) * (s_GU[lm][s][p][c][m] + s_GU[lm][o][p][c][m]), n[m], gn);
+      s_fv[lm][s][p][c] = w * (pavg * n[c] - A.nu * gn + A.nu * tau_f * jump[c]);
+    }
+    s_fv[lm][s][p][D] = -T(0.5) * w * jn;
+    // -nu/2 [[u]] (x) n in reference coordinates: Fx[c][r] = sum_m Ji[r][m] F[c][m]
+    T jin[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      T t = T(0);
+#pragma unroll
+      for (int m = 0; m < D; ++m) t = fma(s_Ji[lm][s][p][r][m], n[m], t);
+      jin[r] = t;
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int r = 0; r < D; ++r) s_Fx[lm][s][p][c][r] = -T(0.5) * w * A.nu * jump[c] * jin[r];
+  }
+  __syncthreads();
+  // ---- phase 4: integrate against the test functions of node a on side s
+  if (!active) return;
+  const int a0 = a % N, a1 = (a / N) % N, a2 = a / (N * N);
+  T out[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) out[f] = T(0);
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int ia = p % N, iz = (D == 3) ? p / N : 0;
+    const T l2 = (D == 3) ? tb.B[iz][a2] : T(1);
+    const T d2 = (D == 3) ? tb.Dn[iz][a2] : T(0);
+    const T l1 = s_L1[lm][s][ia][a1], dl1 = s_dL1[lm][s][ia][a1];
+    const T phi = L0[a0] * l1 * l2;
+    const T dphi[3] = {dL0[a0] * l1 * l2, L0[a0] * dl1 * l2, L0[a0] * l1 * d2};
+    if (MODE == 0) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        T acc = phi * s_fv[lm][s][p][c];
+#pragma unroll
+        for (int r = 0; r < D; ++r) acc = fma(dphi[r], s_Fx[lm][s][p][c][r], acc);
+        out[c] += acc;
+      }
+      out[D] = fma(phi, s_fv[lm][s][p][D], out[D]);
+    } else {
+      // diagonal: w [ -nu phi (grad phi . n_s) + nu tau phi^2 ] for each velocity component
+      const double ang = A.mc_ang[mc * N + ia];
+      double wd = A.mc_w[mc * N + ia];
+      if (D == 3) wd *= (double)TabSel<double>::get(K).w[iz] * A.dz;
+      const T w = (T)wd;
+      const T sg = (s == 0) ? T(1) : T(-1);
+      const T n[3] = {sg * (T)cos(ang), sg * (T)sin(ang), T(0)};
+      T gn = T(0);
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        T g = T(0);
+#pragma unroll
+        for (int r = 0; r < D; ++r) g = fma(dphi[r], s_Ji[lm][s][p][r][m], g);
+        gn = fma(g, n[m], gn);
+      }
+      const T dv = w * A.nu * (tau_f * phi * phi - phi * gn);
+#pragma unroll
+      for (int c = 0; c < D; ++c) out[c] += dv;
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) atomicAdd(&A.dst[(int64_t)node * NF + f], out[f]);
+}
+
+}  // namespace mf

@@ -1,0 +1,228 @@
+// Element-wise and reduction kernels: history term, Dirichlet rows, casts,
+// the cell part of diag(J) (Algorithm 1 written as a direct sum per local DoF),
+// and the vector kernels of the Krylov solver (FP64 dots/axpys for CGS2).
+#pragma once
+#include "mf_cell.cuh"
+
+namespace mf {
+
+// h_t = (alpha_1 u^n + alpha_2 u^{n-1}) / dt
+__global__ void k_history(const double* __restrict__ un, const double* __restrict__ unm1, double* __restrict__ ht,
+                          int64_t n, double c1, double c2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ht[i] = c1 * un[i] + (unm1 ? c2 * unm1[i] : 0.0);
+}
+
+// Jacobian: identity rows on wall velocity DoFs (y = x there).
+template <int D, typename T>
+__global__ void k_dirichlet_copy(const int32_t* __restrict__ wall, int64_t nw, const T* __restrict__ x, T* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nw) return;
+  const int64_t n = wall[i];
+#pragma unroll
+  for (int c = 0; c < D; ++c) y[n * (D + 1) + c] = x[n * (D + 1) + c];
+}
+// Residual: r = u - g on wall velocity DoFs.
+template <int D>
+__global__ void k_dirichlet_res(const int32_t* __restrict__ wall, int64_t nw, const double* __restrict__ up,
+                                const double* __restrict__ g, double* __restrict__ r) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nw) return;
+  const int64_t n = wall[i];
+#pragma unroll
+  for (int c = 0; c < D; ++c) r[n * (D + 1) + c] = up[n * (D + 1) + c] - (g ? g[n * D + c] : 0.0);
+}
+// diag = 1 on wall velocity DoFs.
+template <int D, typename T>
+__global__ void k_dirichlet_one(const int32_t* __restrict__ wall, int64_t nw, T* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nw) return;
+  const int64_t n = wall[i];
+#pragma unroll
+  for (int c = 0; c < D; ++c) y[n * (D + 1) + c] = T(1);
+}
+
+template <typename A, typename B>
+__global__ void k_cast(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (B)a[i];
+}
+
+// ---------------------------------------------------------------------------
+// Cell part of diag(J): for each local DoF (node a, field f) the entry of the
+// element matrix of blocks A-hat (velocity) and D-hat (pressure) on the
+// diagonal, summed over the Gauss points from the linearisation cache.
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(CellCfg<D, K>::THREADS)
+k_cell_diag(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__ cache, T* __restrict__ diag,
+            T nu, T a0dt) {
+  using C = CellCfg<D, K>;
+  constexpr int N = C::N, NQ = C::NQ, NF = D + 1;
+  using CF = Cache<D>;
+  __shared__ SmTab<N, T> st;
+  load_tab<K, T>(st);
+  __syncthreads();
+  const int cl = threadIdx.x / NQ, t = threadIdx.x % NQ;
+  const int64_t cell = (int64_t)blockIdx.x * C::CPB + cl;
+  if (cell >= nc) return;
+  const int ai[3] = {t % N, (t / N) % N, t / (N * N)};
+  const int64_t P = nc * NQ;
+  T dsum[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) dsum[f] = T(0);
+  for (int q = 0; q < NQ; ++q) {
+    const int qi[3] = {q % N, (q / N) % N, q / (N * N)};
+    T bv[3], dvv[3], hv[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      bv[u] = u < D ? st.B[qi[u]][ai[u]] : T(1);
+      dvv[u] = u < D ? st.Dn[qi[u]][ai[u]] : T(0);
+      hv[u] = u < D ? st.Hn[qi[u]][ai[u]] : T(0);
+    }
+    const T phi = bv[0] * bv[1] * bv[2];
+    T dphi[D], Hphi[Sym<D>::n];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      T p = T(1);
+#pragma unroll
+      for (int u = 0; u < D; ++u) p *= (u == r) ? dvv[u] : bv[u];
+      dphi[r] = p;
+    }
+#pragma unroll
+    for (int e = 0; e < Sym<D>::n; ++e) {
+      const int r = sym_r(D, e), s = sym_s(D, e);
+      T p = T(1);
+#pragma unroll
+      for (int u = 0; u < D; ++u) p *= (r == s) ? (u == r ? hv[u] : bv[u]) : ((u == r || u == s) ? dvv[u] : bv[u]);
+      Hphi[e] = p;
+    }
+    const T* cp = cache + cell * NQ + q;
+    T Ji[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int m = 0; m < D; ++m) Ji[r][m] = cp[(CF::JINV + r * D + m) * P];
+    const T Wq = cp[CF::W * P];
+    T gphi[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      T s = T(0);
+#pragma unroll
+      for (int r = 0; r < D; ++r) s = fma(dphi[r], Ji[r][m], s);
+      gphi[m] = s;
+    }
+    T lap = T(0);
+#pragma unroll
+    for (int e = 0; e < Sym<D>::n; ++e) lap = fma(cp[(CF::G + e) * P], Hphi[e], lap);
+#pragma unroll
+    for (int r = 0; r < D; ++r) lap = fma(-cp[(CF::CT + r) * P], dphi[r], lap);
+    T sa = T(0), g2 = T(0);
+#pragma unroll
+    for (int m = 0; m < D; ++m) { sa = fma(cp[(CF::A + m) * P], gphi[m], sa); g2 = fma(gphi[m], gphi[m], g2); }
+    const T tau = cp[CF::TAU * P];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const T guc = cp[(CF::GU + c * D + c) * P];
+      const T lb = a0dt * phi + sa + guc * phi;
+      T e = phi * lb + nu * g2 + tau * sa * (lb - nu * lap) + tau * phi * gphi[c] * cp[(CF::RS + c) * P];
+      dsum[c] = fma(Wq, e, dsum[c]);
+    }
+    dsum[D] = fma(Wq * tau, g2, dsum[D]);
+  }
+  int id = cells[cell * NQ + t];
+  const int64_t node = id < 0 ? ~id : id;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) atomicAdd(&diag[node * NF + f], dsum[f]);
+}
+
+// ---------------------------------------------------------------------------
+// Krylov vector kernels (grid-stride).
+template <typename T>
+__global__ void k_axpby(int64_t n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+// y = x * s / *scal  (scal read on the device: no host round trip)
+__global__ void k_scale_by(int64_t n, const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ nrm2) {
+  const double inv = 1.0 / sqrt(*nrm2);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * inv;
+}
+template <typename T>
+__global__ void k_mul(int64_t n, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a[i] * b[i];
+}
+template <typename T>
+__global__ void k_recip(int64_t n, const T* __restrict__ a, T* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = T(1) / a[i];
+}
+
+// Partial dot products: part[i][blockIdx.x] = sum over the block's range of V_i . w
+// (V_i = V + i * ldv), one grid row per vector (blockIdx.y = i).
+__global__ void k_mdot_part(int64_t n, const double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
+                            double* __restrict__ part) {
+  const int i = blockIdx.y;
+  const double* v = V + (int64_t)i * ldv;
+  double s = 0.0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    s = fma(v[j], w[j], s);
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[(int64_t)i * gridDim.x + blockIdx.x] = s;
+  }
+}
+// out[i] (+)= sum_b part[i][b]  (one block per vector, fixed order: deterministic)
+__global__ void k_mdot_final(const double* __restrict__ part, int nb, double* __restrict__ out, int accumulate) {
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(int64_t)i * nb + b];
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[i] = accumulate ? out[i] + s : s;
+  }
+}
+// w -= sum_{i<m} h[i] V_i   (sign = -1) or w += (sign = +1)
+__global__ void k_maxpy(int64_t n, int m, const double* __restrict__ V, int64_t ldv, const double* __restrict__ h,
+                        double sign, double* __restrict__ w) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[j];
+    for (int i = 0; i < m; ++i) s = fma(sign * __ldg(h + i), V[(int64_t)i * ldv + j], s);
+    w[j] = s;
+  }
+}
+// subtract the mean of the pressure component (stride d+1) given its sum
+__global__ void k_sub_pmean(int64_t nn, int nf, double* __restrict__ v, const double* __restrict__ psum) {
+  const double mean = *psum / (double)nn;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x)
+    v[i * nf + nf - 1] -= mean;
+}
+// sum of the pressure component, partials per block
+__global__ void k_psum_part(int64_t nn, int nf, const double* __restrict__ v, double* __restrict__ part) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x)
+    s += v[i * nf + nf - 1];
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+}  // namespace mf

@@ -1,0 +1,119 @@
+"""GPU parity: the CUDA library against the CPU FP64 oracle on the same seeded inputs.
+
+Bars (normwise, ||y_gpu - y_oracle||_2 / ||y_oracle||_2): 1e-12 for FP64 applies,
+residuals and diagonals; 1e-5 for FP32 applies.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests.oracle_helpers import make_op
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def setup(d, k, m, n_r, n_s, n_z=1, bdf=2, theta=0.137, nu=0.05, omega=1.0, dt=0.01, state="iid", seed=11):
+    from paper_2608_27423_b300 import RotorStatorOperator
+    mesh, prm, f = synth.make_config(d=d, k=k, m=m, n_r=n_r, n_s=n_s, n_z=n_z, nu=nu, omega=omega, dt=dt, bdf=bdf,
+                                     theta=theta, state=state, seed=seed)
+    op = make_op(mesh, prm, f)
+    g = RotorStatorOperator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
+    dev = torch.device("cuda")
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    g.set_history(T(f["u_n"]), T(f["u_nm1"]) if f["u_nm1"] is not None else None)
+    g.set_linearization(T(f["up_star"]), prm["theta"])
+    return mesh, prm, f, op, g, T
+
+
+CASES = [
+    dict(d=2, k=2, m=4, n_r=2, n_s=3),
+    dict(d=2, k=3, m=2, n_r=2, n_s=2, bdf=1),
+    dict(d=2, k=1, m=4, n_r=2, n_s=3),
+    dict(d=2, k=4, m=2, n_r=1, n_s=2),
+    dict(d=3, k=2, m=2, n_r=1, n_s=2, n_z=3),
+    dict(d=3, k=3, m=1, n_r=1, n_s=2, n_z=2, theta=0.9),
+    dict(d=3, k=1, m=2, n_r=2, n_s=2, n_z=3),
+]
+
+
+@pytest.mark.parametrize("c", CASES, ids=lambda c: f"d{c['d']}k{c['k']}")
+def test_jacobian_fp64_matches_oracle(c):
+    mesh, prm, f, op, g, T = setup(**c)
+    y_ref = op.apply(f["x"])
+    y = torch.empty_like(T(f["x"]))
+    g.apply_jacobian(T(f["x"]), y)
+    assert rel(y.cpu().numpy(), y_ref) <= TOL64
+
+
+@pytest.mark.parametrize("c", CASES, ids=lambda c: f"d{c['d']}k{c['k']}")
+def test_residual_matches_oracle(c):
+    mesh, prm, f, op, g, T = setup(**c)
+    up = f["up_star"] * 0.7 + 0.1
+    r_ref = op.residual(up)
+    r = torch.empty_like(T(up))
+    g.residual(T(up), r)
+    assert rel(r.cpu().numpy(), r_ref) <= TOL64
+
+
+@pytest.mark.parametrize("c", CASES[:5], ids=lambda c: f"d{c['d']}k{c['k']}")
+def test_jacobian_fp32_matches_oracle(c):
+    mesh, prm, f, op, g, T = setup(**c)
+    y_ref = op.apply(f["x"])
+    x32 = T(f["x"]).float()
+    y = torch.empty_like(x32)
+    from paper_2608_27423_b300 import MF_FP32
+    g.apply_jacobian(x32, y, prec=MF_FP32)
+    assert rel(y.double().cpu().numpy(), y_ref) <= TOL32
+
+
+@pytest.mark.parametrize("c", CASES[:5], ids=lambda c: f"d{c['d']}k{c['k']}")
+def test_diagonal_matches_assembled(c):
+    mesh, prm, f, op, g, T = setup(**c)
+    dref = op.diagonal()
+    dg = torch.empty_like(T(f["x"]))
+    g.diagonal(dg)
+    assert rel(dg.cpu().numpy(), dref) <= TOL64
+
+
+def test_node_coordinates_follow_rotation():
+    mesh, prm, f, op, g, T = setup(d=3, k=2, m=2, n_r=1, n_s=2, n_z=2, theta=1.3)
+    x = torch.empty((mesh.n_nodes, 3), dtype=torch.float64, device="cuda")
+    g.node_coords(x)
+    assert np.abs(x.cpu().numpy() - op.prob.x).max() < 1e-14
+
+
+@pytest.mark.parametrize("theta", [0.0, 1e-9, 2 * np.pi / 8 * 3, 2 * np.pi / 8 * 3 + 1e-11, -0.4, 7.0])
+def test_mortar_angles_edge_cases(theta):
+    """Conforming angles (zero-length halves), near-conforming, negative and >2pi angles."""
+    mesh, prm, f, op, g, T = setup(d=2, k=2, m=2, n_r=1, n_s=2, theta=theta)
+    y_ref = op.apply(f["x"])
+    y = torch.empty_like(T(f["x"]))
+    g.apply_jacobian(T(f["x"]), y)
+    assert rel(y.cpu().numpy(), y_ref) <= TOL64
+
+
+def test_apply_is_deterministic_to_roundoff():
+    mesh, prm, f, op, g, T = setup(d=3, k=2, m=2, n_r=1, n_s=2, n_z=3)
+    x = T(f["x"])
+    y1 = torch.empty_like(x)
+    y2 = torch.empty_like(x)
+    g.apply_jacobian(x, y1)
+    g.apply_jacobian(x, y2)
+    assert float((y1 - y2).norm() / y1.norm()) < 1e-14
+
+
+def test_apply_before_linearization_is_an_error():
+    from paper_2608_27423_b300 import RotorStatorOperator, MfError
+    mesh, prm, f = synth.make_config(d=2, k=2, m=2, n_r=1, n_s=2, nu=0.1, omega=1.0, dt=0.01, bdf=1, theta=0.1)
+    g = RotorStatorOperator(mesh, 0.1, 1.0, 0.01, 1)
+    x = torch.zeros(mesh.n_dofs, dtype=torch.float64, device="cuda")
+    with pytest.raises(MfError):
+        g.apply_jacobian(x, torch.empty_like(x))
