@@ -1,0 +1,356 @@
+"""Benchmark: Jacobian-apply throughput of the rotor-stator operator on B300.
+
+Workload (default): 3D rotor-stator cylinder, 137,088 Q2 hexes (m=28, n_r=9,
+n_s=18, n_z=36), 4,546,148 DoFs, Re=200 (nu = 1/(400 pi), omega = 1), BDF2,
+dt = 0.005, rotor at theta = 0.137, smooth low-mode linearisation state,
+FP64.  One step = one full Jacobian apply y = J x (cell kernel, mortar face
+kernel, Dirichlet rows) with the per-point linearisation already cached.
+The working set (1.1 GB cache + vectors) exceeds the 126 MB L2.
+
+Prints one JSON line.  --impl reference times the CPU FP64 oracle instead
+(matrix-free path on a bounded sample of cells and mortar cells).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Jacobian-apply DoFs/s (FP64 vs FP32) at Q2/Q3; time to 1e-8 residual per step"
+FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (non-tensor) nominal
+FP64_PROBE_TFLOPS = 1.128        # FMA-chain probe on the B300s
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default="3d_q2")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def algorithmic_flops_per_cell(d, k):
+    """FP64 operations (FMA = 2) of one cell in the Jacobian kernel, counted from
+    its loops: sum factorisation (interpolation, gradients, Hessians, the two
+    transposed passes) and the point physics."""
+    n = k + 1
+    nf = d + 1
+    sym = d * (d + 1) // 2
+    sumfact_fma = 4 * d * nf * n + sym * d * n
+    fma_pt = (nf * d * d) + d * (sym + d) + d * 2 * d + d + d * d * 2 + d * d * d + d * d
+    oth_pt = d + d + d * d * 2 + d + 2 * d + 1 + d * d + 1 + d
+    per_pt = 2 * (sumfact_fma + fma_pt) + oth_pt
+    return per_pt * n ** d
+
+
+def algorithmic_bytes_per_launch(d, k, n_cells, n_nodes, ncache, prec_bytes=8):
+    """Bytes the cell kernel must move once: the per-point cache, the cell->node
+    table, src read once per node, dst read+written once per node."""
+    nq = (k + 1) ** d
+    return n_cells * nq * (ncache * prec_bytes + 4) + n_nodes * (d + 1) * prec_bytes * 3
+
+
+class ClockSampler:
+    def __init__(self, out_path):
+        self.path = out_path
+        self.p = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
+        except Exception:
+            self.p = None
+
+    def stop(self, dev_index=0):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != dev_index:
+                continue
+            rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def build_inputs(workload):
+    import synth
+    mesh, prm, f = synth.make_config(workload)
+    return mesh, prm, f
+
+
+# --------------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(mesh, prm, f, seconds):
+    """Oracle matrix-free Jacobian apply on a bounded sample (cells and mortar
+    cells of the first z-layers), scaled to whole-operator DoFs/s."""
+    from oracle.fem import Problem
+    from oracle.mortar import Mortar
+    prob = Problem(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"], prm["theta"])
+    prob.set_history(f["u_n"], f["u_nm1"])
+    d = mesh.d
+    cmask = np.zeros((mesh.n_nodes, d + 1), bool)
+    cmask[mesh.wall.astype(bool), :d] = True
+    xc = np.where(cmask, 0.0, f["x"])
+    nc = mesh.n_cells
+    # volume: grow the sample until the time budget is used
+    t_vol, cells_done, chunk = 0.0, 0, 512
+    out = np.zeros((mesh.n_nodes, d + 1))
+    while t_vol < 0.8 * seconds and cells_done < nc:
+        cl = np.arange(cells_done, min(nc, cells_done + chunk))
+        t0 = time.perf_counter()
+        prob.volume_apply(f["up_star"], xc, cl=cl, out=out)
+        t_vol += time.perf_counter() - t0
+        cells_done += len(cl)
+    # mortar: one z-layer of mortar cells
+    class OneLayer:
+        pass
+    m1 = OneLayer()
+    for key in ("d", "k", "x0", "cells", "cell_side", "node_side", "wall", "R", "n_R", "H", "phi0"):
+        setattr(m1, key, getattr(mesh, key))
+    m1.n_z = mesh.n_z
+    m1.iface_rotor = mesh.iface_rotor
+    m1.iface_stator = mesh.iface_stator
+    prob.mesh = m1
+    t0 = time.perf_counter()
+    mt = Mortar.__new__(Mortar)
+    # build only layer 0 of the mortar (same code path as Mortar.__init__ with n_z = 1)
+    m1.n_z = 1
+    m1.H = mesh.H / mesh.n_z
+    Mortar.__init__(mt, prob)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mt.apply(xc, out=out)
+    t_mort = time.perf_counter() - t0
+    n_layers = mesh.n_z
+    t_full = t_vol * nc / cells_done + (t_mort + t_build) * n_layers
+    rate = mesh.n_dofs / t_full
+    sample = (f"volume apply on {cells_done} of {nc} cells ({t_vol:.1f} s) + mortar build and apply on 1 of "
+              f"{n_layers} z-layers ({t_build + t_mort:.1f} s), scaled to the whole operator")
+    return rate, sample, t_full
+
+
+def cpu_cores_used():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([1] + [i.get("num_threads", 1) for i in info if i.get("user_api") == "blas"])
+    except Exception:
+        return 1
+
+
+# --------------------------------------------------------------------- main
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return main_reference(args, rank, world)
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2608_27423_b300 import RotorStatorOperator, MF_FP32, MF_FP64, solver_defaults, MF_PC_JACOBI, \
+        MF_PC_CHEBYSHEV
+    from paper_2608_27423_b300 import build as _b
+    mesh, prm, f = build_inputs(args.workload)
+    dev = torch.device("cuda", local)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    op = RotorStatorOperator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
+    up_star = T(f["up_star"])
+    op.set_history(T(f["u_n"]), T(f["u_nm1"]) if f["u_nm1"] is not None else None)
+    op.set_linearization(up_star, prm["theta"])
+    x = T(f["x"])
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    n_dofs = op.n_dofs
+    d, k = mesh.d, mesh.k
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # ---- FP64 apply: the headline
+    sampler = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    for _ in range(args.warmup):
+        op.apply_jacobian(x, y)
+    torch.cuda.synchronize()
+    sampler.start()
+    op.profile(True)
+    ms = timed(lambda: op.apply_jacobian(x, y), args.steps, 0)
+    prof = op.profile_read()
+    op.profile(False)
+    clocks = sampler.stop(local)
+    t_max = ms
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_step = t_max / args.steps
+    value = n_dofs * world / (ms_step * 1e-3)
+
+    # dominant kernel roofline (FP64 cell Jacobian, bound by the FP64 pipe)
+    nl, kms = prof["cell_jac_fp64"]
+    k_ms = kms / max(nl, 1)
+    flops = algorithmic_flops_per_cell(d, k) * op.n_cells
+    ncache = (d * d + 1 + d * (d + 1) // 2 + d + d + d * d + d + 1)
+    byts = algorithmic_bytes_per_launch(d, k, op.n_cells, op.n_nodes, ncache)
+    achieved_tf = flops / (k_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
+                "kernel": f"k_cell_jac<{d},{k},double>", "kernel_ms": round(k_ms, 4),
+                "flops_per_launch": flops, "peak_source": "recipe nominal FP64 1.25 TFLOP/s (probe 1.128)",
+                "hbm": {"achieved_gbs": round(byts / (k_ms * 1e-3) / 1e9, 1),
+                        "algorithmic_bytes": byts}}
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        pk = json.load(open(peaks_path))
+        roofline["hbm"]["peak_gbs"] = pk.get("hbm_gbs")
+        roofline["hbm"]["frac"] = round(roofline["hbm"]["achieved_gbs"] / pk["hbm_gbs"], 4)
+    shares = {kk: {"launches": v[0], "ms": round(v[1], 3)} for kk, v in prof.items() if v[0]}
+
+    extra = {}
+    # ---- FP32 apply
+    x32 = x.float()
+    y32 = torch.empty_like(x32)
+    ms32 = timed(lambda: op.apply_jacobian(x32, y32, prec=MF_FP32), args.steps, 3)
+    extra["fp32_apply_dofs_per_s"] = n_dofs / (ms32 / args.steps * 1e-3)
+    # ---- residual and linearisation set-up
+    r = torch.empty_like(x)
+    msr = timed(lambda: op.residual(up_star, r), max(10, args.steps // 10), 2)
+    extra["residual_dofs_per_s"] = n_dofs / (msr / max(10, args.steps // 10) * 1e-3)
+    msl = timed(lambda: op.set_linearization(up_star, prm["theta"]), 10, 1)
+    extra["set_linearization_ms"] = msl / 10
+
+    # ---- e2e: host buffers, H2D + apply + D2H per step
+    xh = torch.empty(x.shape, dtype=torch.float64, pin_memory=True)
+    xh.copy_(x.cpu())
+    yh = torch.empty(x.shape, dtype=torch.float64, pin_memory=True)
+    xd = torch.empty_like(x)
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        op.apply_jacobian(xd, y)
+        yh.copy_(y, non_blocking=True)
+    ms_e2e = timed(e2e_step, max(20, args.steps // 5), 2)
+    e2e_steps = max(20, args.steps // 5)
+    e2e = {"value": n_dofs * world / (ms_e2e / e2e_steps * 1e-3), "unit": "DoFs/s",
+           "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(yh.numel() * 8)}
+
+    # ---- nonlinear step to 1e-8: all-FP64 vs mixed precision
+    if not args.no_solve:
+        res = {}
+        for name, pc, pcp in (("fp64_jacobi", MF_PC_JACOBI, MF_FP64), ("mixed_cheb_fp32", MF_PC_CHEBYSHEV, MF_FP32)):
+            up = up_star.clone()
+            o = solver_defaults(theta=prm["theta"], pc=pc, pc_precision=pcp, newton_rtol=1e-8, max_newton=30,
+                                lin_rtol=1e-3, restart=60, max_lin_iters=600, cheb_degree=4)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, rep = op.solve_step(up, o)
+            torch.cuda.synchronize()
+            dt_s = time.perf_counter() - t0
+            res[name] = {"status": int(st), "seconds": round(dt_s, 4), "newton_iters": rep.newton_iters,
+                         "lin_iters_total": rep.lin_iters_total,
+                         "res_reduction": (rep.res_norm[rep.newton_iters] / rep.res_norm[0])
+                         if rep.res_norm[0] > 0 else None}
+            res[name]["solution"] = up
+        a, b = res["fp64_jacobi"].pop("solution"), res["mixed_cheb_fp32"].pop("solution")
+        res["rel_solution_diff_mixed_vs_fp64"] = float((a - b).norm() / a.norm())
+        extra["solve_to_1e-8"] = res
+        op.set_linearization(up_star, prm["theta"])
+
+    line = {"metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: 3D rotor-stator cylinder, {op.n_cells} Q{k} hexes, "
+                                   f"{n_dofs} DoFs, Re=200, BDF2 dt=0.005, theta=0.137, FP64 Jacobian apply",
+                       "n_cells": op.n_cells, "n_dofs": n_dofs, "k": k, "d": d,
+                       "l2": "inputs larger than L2 (per-point cache ~1.1 GB)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline, "kernel_shares": shares, "gpu_launches": 3 * args.steps,
+            "e2e": e2e, "clocks": clocks, **extra}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, sample, t_full = cpu_oracle_rate(mesh, prm, f, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "DoFs/s", "cores": cpu_cores_used(), "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line, default=float), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main_reference(args, rank, world):
+    if rank != 0:
+        return
+    mesh, prm, f = build_inputs(args.workload)
+    budget = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    rates = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        rate, sample, t_full = cpu_oracle_rate(mesh, prm, f, budget)
+        if i >= args.warmup:
+            rates.append(rate)
+    value = float(np.median(rates))
+    cores = cpu_cores_used()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mesh.n_dofs / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: CPU FP64 oracle, matrix-free path", "n_dofs": mesh.n_dofs},
+            "cpu_baseline": {"value": value, "unit": "DoFs/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DoFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -123,6 +123,16 @@ class RotorStatorOperator:
     def diagonal(self, out, prec=MF_FP64, stream=None):
         self._chk(self.lib.mf_diagonal(self.h, _ptr(out), int(prec), _stream(stream)), "mf_diagonal")
 
+    def profile(self, enable=True):
+        """Enable (and reset) or disable the per-kernel CUDA-event timers."""
+        self._chk(self.lib.mf_profile(self.h, int(bool(enable))), "mf_profile")
+
+    def profile_read(self):
+        """{kernel kind: (launches, total device ms)} since the last reset (synchronising)."""
+        pr = _lib.MfProfile()
+        self._chk(self.lib.mf_profile_read(self.h, C.byref(pr)), "mf_profile_read")
+        return {k: (pr.launches[i], pr.ms[i]) for i, k in enumerate(_lib.PROF_KINDS)}
+
     def solve_step(self, up, opts=None, stream=None):
         rep = MfSolveReport()
         o = opts if opts is not None else solver_defaults()

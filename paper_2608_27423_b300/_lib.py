@@ -17,7 +17,10 @@ MF_PC_JACOBI, MF_PC_CHEBYSHEV = 0, 1
 # every symbol include/mf.h declares
 EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_create", "mf_destroy", "mf_last_error", "mf_sizes",
            "mf_set_angle", "mf_node_coords", "mf_dirichlet", "mf_set_history", "mf_set_linearization",
-           "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step"]
+           "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step",
+           "mf_profile", "mf_profile_read"]
+PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
+              "cell_linearization", "dirichlet", "diagonal"]
 
 
 class MfOptions(C.Structure):
@@ -35,6 +38,10 @@ class MfSolveReport(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("lin_iters_total", C.c_int), ("lin_iters", C.c_int * 64),
                 ("res_norm", C.c_double * 65), ("lambda_max", C.c_double), ("seconds", C.c_double),
                 ("status", C.c_int)]
+
+
+class MfProfile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
 
 
 class MfError(RuntimeError):
@@ -73,6 +80,8 @@ def load():
     lib.mf_solver_defaults.argtypes = [C.POINTER(MfSolverOpts)]
     lib.mf_solver_defaults.restype = None
     lib.mf_solve_step.argtypes = [vp, vp, C.POINTER(MfSolverOpts), C.POINTER(MfSolveReport), vp]
+    lib.mf_profile.argtypes = [vp, i32]
+    lib.mf_profile_read.argtypes = [vp, C.POINTER(MfProfile)]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("mf_mesh_free", "mf_last_error", "mf_solver_defaults"):

@@ -51,7 +51,16 @@ struct Workspace {
   double* pinned = nullptr;  // host [m+2]
 };
 
+struct ProfEvent {
+  cudaEvent_t a, b;
+  int kind;
+};
+
 struct mf_ctx {
+  bool prof = false;
+  std::vector<ProfEvent> prof_ev;      // pending event pairs
+  std::vector<cudaEvent_t> ev_pool;    // reusable events
+  mf_profile_t prof_acc;
   int d = 0, k = 0;
   int64_t nn = 0, nc = 0, ndof = 0;
   double nu = 0, omega = 0, dt = 0, a0dt = 0, inv_dt2 = 0, alpha[3] = {0, 0, 0}, F = 1.0;
@@ -77,6 +86,21 @@ struct mf_ctx {
 };
 
 static bool g_tabs_ready[64] = {false};
+
+// Profiling: a scope that records an event pair around one launch when enabled.
+static cudaEvent_t pool_get(mf_ctx* h) {
+  if (!h->ev_pool.empty()) { cudaEvent_t e = h->ev_pool.back(); h->ev_pool.pop_back(); return e; }
+  cudaEvent_t e; cudaEventCreate(&e); return e;
+}
+struct ProfScope {
+  mf_ctx* h; int kind; cudaStream_t st; cudaEvent_t a = nullptr;
+  ProfScope(mf_ctx* h_, int kind_, cudaStream_t st_) : h(h_), kind(kind_), st(st_) {
+    if (h->prof) { a = pool_get(h); cudaEventRecord(a, st); }
+  }
+  ~ProfScope() {
+    if (h->prof && a) { cudaEvent_t b = pool_get(h); cudaEventRecord(b, st); h->prof_ev.push_back({a, b, kind}); }
+  }
+};
 
 #define CK(call)                                                                       \
   do {                                                                                 \
@@ -131,6 +155,7 @@ static void launch_state(mf_ctx* h, int mode, const double* up, double* dst, cud
   A.cache = h->cache64; A.dst = dst; A.nu = h->nu; A.omega = h->omega; A.a0dt = h->a0dt; A.inv_dt2 = h->inv_dt2;
   using C = CellCfg<D, K>;
   const unsigned g = nblk(h->nc, C::CPB);
+  ProfScope ps(h, mode == 0 ? 5 : 4, st);
   if (mode == 0) k_cell_state<D, K, 0><<<g, C::THREADS, 0, st>>>(A);
   else k_cell_state<D, K, 1><<<g, C::THREADS, 0, st>>>(A);
 }
@@ -139,6 +164,7 @@ template <int D, int K, typename T>
 static void launch_jac(mf_ctx* h, const T* cache, const T* x, T* y, cudaStream_t st) {
   using C = CellCfg<D, K>;
   const unsigned g = nblk(h->nc, C::CPB);
+  ProfScope ps(h, std::is_same<T, double>::value ? 0 : 1, st);
   k_cell_jac<D, K, T><<<g, C::THREADS, 0, st>>>(h->cells, h->nc, cache, x, y, (T)h->nu, (T)h->a0dt);
 }
 
@@ -150,6 +176,7 @@ static void launch_mortar(mf_ctx* h, int mode, const T* src, T* dst, int zero_wa
   A.dz = h->H / h->n_z; A.zero_wall = zero_wall;
   using C = MortarCfg<D, K>;
   const unsigned g = nblk(h->nm, C::MPB);
+  ProfScope ps(h, mode == 1 ? 7 : (std::is_same<T, double>::value ? 2 : 3), st);
   if (mode == 0) k_mortar<D, K, T, 0><<<g, C::THREADS, 0, st>>>(A);
   else k_mortar<D, K, T, 1><<<g, C::THREADS, 0, st>>>(A);
 }
@@ -157,6 +184,7 @@ static void launch_mortar(mf_ctx* h, int mode, const T* src, T* dst, int zero_wa
 template <int D, int K, typename T>
 static void launch_cell_diag(mf_ctx* h, const T* cache, T* diag, cudaStream_t st) {
   using C = CellCfg<D, K>;
+  ProfScope ps(h, 7, st);
   k_cell_diag<D, K, T><<<nblk(h->nc, C::CPB), C::THREADS, 0, st>>>(h->cells, h->nc, cache, diag, (T)h->nu, (T)h->a0dt);
 }
 
@@ -219,6 +247,8 @@ static void free_ws(Workspace& w) {
 
 extern "C" mf_status mf_destroy(mf_handle h) {
   if (!h) return MF_ERR_ARG;
+  for (auto& e : h->prof_ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
   void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
                   h->mc_cell, h->mc_tau, h->mc_xi, h->mc_ang, h->mc_w, h->ht, h->g, h->cache64, h->cache32};
   for (void* p : ptrs) if (p) cudaFree(p);
@@ -381,6 +411,7 @@ static mf_status apply_t(mf_ctx* h, const T* x, T* y, cudaStream_t st) {
   MF_DISPATCH(h->d, h->k, (launch_jac<D, K, T>(h, cache, x, y, st)));
   MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 0, x, y, 1, st)));
   if (h->nwall) {
+    ProfScope ps(h, 6, st);
     if (h->d == 2) k_dirichlet_copy<2, T><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, x, y);
     else k_dirichlet_copy<3, T><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, x, y);
   }
@@ -416,6 +447,31 @@ extern "C" mf_status mf_diagonal(mf_handle h, void* diag_out, mf_precision prec,
   if (prec == MF_FP64) return diag_t<double>(h, (double*)diag_out, S(stream));
   if (prec == MF_FP32) return diag_t<float>(h, (float*)diag_out, S(stream));
   return MF_ERR_ARG;
+}
+
+extern "C" mf_status mf_profile(mf_handle h, int enable) {
+  if (!h) return MF_ERR_ARG;
+  for (auto& e : h->prof_ev) { h->ev_pool.push_back(e.a); h->ev_pool.push_back(e.b); }
+  h->prof_ev.clear();
+  std::memset(&h->prof_acc, 0, sizeof(h->prof_acc));
+  h->prof = enable != 0;
+  return MF_OK;
+}
+
+extern "C" mf_status mf_profile_read(mf_handle h, mf_profile_t* out) {
+  if (!h || !out) return MF_ERR_ARG;
+  for (auto& e : h->prof_ev) {
+    CK(cudaEventSynchronize(e.b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e.a, e.b));
+    h->prof_acc.launches[e.kind] += 1;
+    h->prof_acc.ms[e.kind] += ms;
+    h->ev_pool.push_back(e.a);
+    h->ev_pool.push_back(e.b);
+  }
+  h->prof_ev.clear();
+  *out = h->prof_acc;
+  return MF_OK;
 }
 
 #include "mf_solve.inc"

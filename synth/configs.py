@@ -8,6 +8,8 @@
   omega=1; BDF2, dt=0.005; smooth low-mode state.
 * ``3d_q3``: same cylinder, m=22, n_r=7, n_s=14, n_z=25 -> 58,300 hexes, Q3
   (6.5M DoFs); Re = 200.
+* ``3d_q2_mid``: the 3d_q2 physics on m=12, n_r=4, n_s=8, n_z=36 (25,920 hexes,
+  0.86M DoFs; per-point cache 196 MB, still larger than L2) for profiling.
 * small variants for tests.
 """
 import numpy as np
@@ -20,6 +22,8 @@ CONFIGS = {
                   theta=0.137, state="iid"),
     "3d_q2": dict(d=3, k=2, m=28, n_r=9, n_s=18, n_z=36, nu=1.0 / (400.0 * np.pi), omega=1.0,
                   dt=0.005, bdf=2, theta=0.137, state="smooth"),
+    "3d_q2_mid": dict(d=3, k=2, m=12, n_r=4, n_s=8, n_z=36, nu=1.0 / (400.0 * np.pi), omega=1.0,
+                      dt=0.005, bdf=2, theta=0.137, state="smooth"),
     "3d_q3": dict(d=3, k=3, m=22, n_r=7, n_s=14, n_z=25, nu=1.0 / (400.0 * np.pi), omega=1.0,
                   dt=0.005, bdf=2, theta=0.137, state="smooth"),
 }

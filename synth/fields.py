@@ -41,10 +41,18 @@ def smooth_nodal_field(x, ncomp, seed, modes=4):
     draws = splitmix64_uniform(seed, 2 * ncomp * nm)
     amp = (2.0 * draws[: ncomp * nm] - 1.0).reshape(ncomp, nm) / (1.0 + (M ** 2).sum(1))[None]
     ph = (2.0 * np.pi * draws[ncomp * nm:]).reshape(ncomp, nm)
+    # sum_m a cos(pi m.x + ph) = Re sum_m (a e^{i ph}) prod_r e^{i pi m_r x_r}: evaluated as a
+    # tensor contraction over the per-axis exponentials (same values up to roundoff)
+    coef = (amp * np.exp(1j * ph)).reshape((ncomp,) + (modes,) * d)
     out = np.zeros((x.shape[0], ncomp))
     chunk = 1 << 16
+    j = np.arange(modes)
     for s0 in range(0, x.shape[0], chunk):
-        arg = np.pi * x[s0:s0 + chunk] @ M.T                                   # [n, nm]
-        for c in range(ncomp):
-            out[s0:s0 + chunk, c] = (np.cos(arg + ph[c][None]) * amp[c][None]).sum(1)
+        xs = x[s0:s0 + chunk]
+        E = [np.exp(1j * np.pi * xs[:, r:r + 1] * j[None, :]) for r in range(d)]      # [n, modes]
+        if d == 2:
+            val = np.einsum("cab,pa,pb->pc", coef, E[0], E[1])
+        else:
+            val = np.einsum("cabe,pa,pb,pe->pc", coef, E[0], E[1], E[2], optimize=True)
+        out[s0:s0 + chunk] = val.real
     return out
