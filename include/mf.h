@@ -140,7 +140,15 @@ mf_status mf_apply_jacobian(mf_handle h, const void* x, void* y, mf_precision pr
 mf_status mf_diagonal(mf_handle h, void* diag_out, mf_precision prec, void* stream);
 
 /* ---------------------------------------------------------------- solve */
-typedef enum { MF_PC_JACOBI = 0, MF_PC_CHEBYSHEV = 1 } mf_pc_kind;
+/* Preconditioners of the outer FGMRES:
+ *   MF_PC_JACOBI     z = D^-1 v
+ *   MF_PC_CHEBYSHEV  degree-s Chebyshev-Jacobi polynomial on [cheb_lo, 1.1] * lambda_max(D^-1 J)
+ *   MF_PC_GMRES      inner_iters steps of Jacobi-preconditioned GMRES (zero initial guess, CGS2)
+ *   MF_PC_MG         one V-cycle of the multigrid hierarchy attached with mf_mg_attach (Section 3.4):
+ *                    mg_smooth GMRES-Jacobi steps before and after the coarse correction on each
+ *                    level, mg_coarse_iters GMRES-Jacobi steps on the coarsest level; always FP32
+ * each applied with pc_precision operator applies (MF_FP32: the FP32 cache). */
+typedef enum { MF_PC_JACOBI = 0, MF_PC_CHEBYSHEV = 1, MF_PC_GMRES = 2, MF_PC_MG = 3 } mf_pc_kind;
 
 typedef struct {
   double newton_rtol;   /* stop when ||R||_2 <= newton_rtol ||R_0||_2 (default 1e-8) */
@@ -149,11 +157,15 @@ typedef struct {
   double lin_rtol;      /* FGMRES relative tolerance per Newton step (default 1e-4) */
   int    restart;       /* FGMRES restart length (default 50, max 200) */
   int    max_lin_iters; /* total FGMRES iterations per Newton step (default 500) */
-  int    pc;            /* mf_pc_kind (default MF_PC_CHEBYSHEV) */
+  int    pc;            /* mf_pc_kind (default MF_PC_GMRES) */
   int    pc_precision;  /* mf_precision of the preconditioner applies (default MF_FP32) */
   int    cheb_degree;   /* Chebyshev degree (default 4) */
   double cheb_lo;       /* lower end of the Chebyshev interval as a fraction of lambda_max (default 0.1) */
   double theta;         /* rotor angle of this step */
+  int    inner_iters;   /* MF_PC_GMRES inner Krylov dimension (default 20, max 120) */
+  int    line_search;   /* halve the Newton step up to this many times while ||R|| does not decrease (default 6) */
+  int    mg_smooth;     /* MF_PC_MG smoothing steps per level (default 4) */
+  int    mg_coarse_iters; /* MF_PC_MG coarsest-level GMRES dimension (default 40) */
 } mf_solver_opts;
 
 typedef struct {
@@ -176,6 +188,28 @@ void mf_solver_defaults(mf_solver_opts* o);
  * MF_ERR_NAN on failure (up then holds the last iterate). */
 mf_status mf_solve_step(mf_handle h, double* up, const mf_solver_opts* so, mf_solve_report* rep,
                         void* stream);
+
+/* ---------------------------------------------------------------- multigrid
+ * The global-coarsening multigrid of Section 3.4 (geometric and polynomial
+ * coarsening) as a hierarchy of operator handles.  mf_mg_attach links `coarse`
+ * below `fine` (both created by the caller on the same device, same d, nu,
+ * omega, dt, BDF order; the caller keeps both alive while the link is used):
+ *   parent == NULL: polynomial coarsening, same cells and node-free layout,
+ *                   coarse k = fine k - 1;
+ *   parent != NULL: geometric coarsening, equal k; parent[c] (host, [fine
+ *                   cells]) is the coarse cell containing fine cell c and bit r
+ *                   of child[c] is 1 when c is the upper half of it along xi_r.
+ * Coarse levels are linearised at the fine state interpolated to their nodes
+ * during mf_solve_step with pc = MF_PC_MG.  Synchronising.
+ * mf_mg_prolongate / mf_mg_restrict / mf_mg_interpolate expose the transfers
+ * (device FP64 vectors in the interleaved layout of each level):
+ *   prolongate: x_fine = P x_coarse (coarse function at the fine nodes);
+ *   restrict:   r_coarse = P^T-weighted r_fine (transpose with node multiplicities);
+ *   interpolate: u_coarse = fine function at the coarse nodes. */
+mf_status mf_mg_attach(mf_handle fine, mf_handle coarse, const int32_t* parent, const uint8_t* child);
+mf_status mf_mg_prolongate(mf_handle fine, const double* x_coarse, double* x_fine, void* stream);
+mf_status mf_mg_restrict(mf_handle fine, const double* r_fine, double* r_coarse, void* stream);
+mf_status mf_mg_interpolate(mf_handle fine, const double* u_fine, double* u_coarse, void* stream);
 
 /* ---------------------------------------------------------------- profiling
  * Per-kernel CUDA-event timers.  When enabled, every kernel the operator calls

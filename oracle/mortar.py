@@ -98,7 +98,8 @@ def penalty(prob, cell, iface_side):
 class Mortar:
     """Mortar points of the interface at the problem's rotor angle."""
 
-    def __init__(self, prob):
+    def __init__(self, prob, layers=None):
+        """layers: z-layers to build (default all); a subset serves sampled checks."""
         m = prob.mesh
         self.prob = prob
         d = prob.d
@@ -111,7 +112,7 @@ class Mortar:
         phi0 = float(m.phi0)
         self.tau_cell = {}
         recs = []
-        for lz in range(self.n_z):
+        for lz in (range(self.n_z) if layers is None else layers):
             for (pa, L, jr, js) in segs:
                 cr = int(m.iface_rotor[lz, jr])
                 cs = int(m.iface_stator[lz, js])

@@ -9,9 +9,10 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import MF_FP64, MF_FP32, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MfError, MfSolverOpts, MfSolveReport
+from ._lib import MF_FP64, MF_FP32, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
+    MfSolverOpts, MfSolveReport
 
-__all__ = ["RotorStatorOperator", "MF_FP64", "MF_FP32", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MfError",
+__all__ = ["RotorStatorOperator", "MF_FP64", "MF_FP32", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
            "solver_defaults"]
 
 
@@ -123,6 +124,28 @@ class RotorStatorOperator:
     def diagonal(self, out, prec=MF_FP64, stream=None):
         self._chk(self.lib.mf_diagonal(self.h, _ptr(out), int(prec), _stream(stream)), "mf_diagonal")
 
+    def mg_attach(self, coarse, parent=None, child=None):
+        """Link `coarse` as the next multigrid level below this operator (h-coarsening
+        when parent/child maps are given, else p-coarsening k -> k-1)."""
+        if parent is None:
+            st = self.lib.mf_mg_attach(self.h, coarse.h, None, None)
+        else:
+            par = np.ascontiguousarray(parent, dtype=np.int32)
+            chd = np.ascontiguousarray(child, dtype=np.uint8)
+            st = self.lib.mf_mg_attach(self.h, coarse.h, _np_ptr(par), _np_ptr(chd))
+        self._chk(st, "mf_mg_attach")
+        self._coarse = coarse          # keep the coarse level alive while linked
+
+    def mg_prolongate(self, x_coarse, x_fine, stream=None):
+        self._chk(self.lib.mf_mg_prolongate(self.h, _ptr(x_coarse), _ptr(x_fine), _stream(stream)), "mf_mg_prolongate")
+
+    def mg_restrict(self, r_fine, r_coarse, stream=None):
+        self._chk(self.lib.mf_mg_restrict(self.h, _ptr(r_fine), _ptr(r_coarse), _stream(stream)), "mf_mg_restrict")
+
+    def mg_interpolate(self, u_fine, u_coarse, stream=None):
+        self._chk(self.lib.mf_mg_interpolate(self.h, _ptr(u_fine), _ptr(u_coarse), _stream(stream)),
+                  "mf_mg_interpolate")
+
     def profile(self, enable=True):
         """Enable (and reset) or disable the per-kernel CUDA-event timers."""
         self._chk(self.lib.mf_profile(self.h, int(bool(enable))), "mf_profile")
@@ -132,6 +155,9 @@ class RotorStatorOperator:
         pr = _lib.MfProfile()
         self._chk(self.lib.mf_profile_read(self.h, C.byref(pr)), "mf_profile_read")
         return {k: (pr.launches[i], pr.ms[i]) for i, k in enumerate(_lib.PROF_KINDS)}
+
+    def last_error(self):
+        return self.lib.mf_last_error(self.h).decode()
 
     def solve_step(self, up, opts=None, stream=None):
         rep = MfSolveReport()

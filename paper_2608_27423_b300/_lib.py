@@ -12,13 +12,14 @@ MF_OK, MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_OOM, MF_ERR_STATE, MF_ERR_NAN, MF_ERR_NOT
 STATUS_NAMES = ["MF_OK", "MF_ERR_ARG", "MF_ERR_CUDA", "MF_ERR_OOM", "MF_ERR_STATE", "MF_ERR_NAN",
                 "MF_ERR_NOT_CONVERGED", "MF_ERR_BREAKDOWN", "MF_ERR_ITER_LIMIT"]
 MF_FP64, MF_FP32 = 0, 1
-MF_PC_JACOBI, MF_PC_CHEBYSHEV = 0, 1
+MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG = 0, 1, 2, 3
 
 # every symbol include/mf.h declares
 EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_create", "mf_destroy", "mf_last_error", "mf_sizes",
            "mf_set_angle", "mf_node_coords", "mf_dirichlet", "mf_set_history", "mf_set_linearization",
            "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step",
-           "mf_profile", "mf_profile_read"]
+           "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
+           "mf_mg_interpolate"]
 PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
               "cell_linearization", "dirichlet", "diagonal"]
 
@@ -31,7 +32,8 @@ class MfSolverOpts(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_atol", C.c_double), ("max_newton", C.c_int),
                 ("lin_rtol", C.c_double), ("restart", C.c_int), ("max_lin_iters", C.c_int),
                 ("pc", C.c_int), ("pc_precision", C.c_int), ("cheb_degree", C.c_int),
-                ("cheb_lo", C.c_double), ("theta", C.c_double)]
+                ("cheb_lo", C.c_double), ("theta", C.c_double), ("inner_iters", C.c_int),
+                ("line_search", C.c_int), ("mg_smooth", C.c_int), ("mg_coarse_iters", C.c_int)]
 
 
 class MfSolveReport(C.Structure):
@@ -80,6 +82,10 @@ def load():
     lib.mf_solver_defaults.argtypes = [C.POINTER(MfSolverOpts)]
     lib.mf_solver_defaults.restype = None
     lib.mf_solve_step.argtypes = [vp, vp, C.POINTER(MfSolverOpts), C.POINTER(MfSolveReport), vp]
+    lib.mf_mg_attach.argtypes = [vp, vp, vp, vp]
+    lib.mf_mg_prolongate.argtypes = [vp, vp, vp, vp]
+    lib.mf_mg_restrict.argtypes = [vp, vp, vp, vp]
+    lib.mf_mg_interpolate.argtypes = [vp, vp, vp, vp]
     lib.mf_profile.argtypes = [vp, i32]
     lib.mf_profile_read.argtypes = [vp, C.POINTER(MfProfile)]
     for name in EXPORTS:

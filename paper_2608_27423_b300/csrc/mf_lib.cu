@@ -13,6 +13,7 @@
 #include "mf_cell.cuh"
 #include "mf_mortar.cuh"
 #include "mf_small.cuh"
+#include "mf_pmg.cuh"
 
 using namespace mf;
 
@@ -44,11 +45,32 @@ struct Workspace {
   float* f_r = nullptr;
   float* f_d = nullptr;
   float* f_t = nullptr;
+  float* f_w = nullptr;
   double* c_x = nullptr;     // FP64 Chebyshev vectors
   double* c_r = nullptr;
   double* c_d = nullptr;
   double* c_t = nullptr;
   double* pinned = nullptr;  // host [m+2]
+  double* utrial = nullptr;  // [n] Newton line-search trial state
+  double* ep = nullptr;      // [n] normalised constant-pressure vector
+  double* jep = nullptr;     // [n] J e_p
+  int mi32 = 0, mi64 = 0;    // inner GMRES dimensions allocated
+  int part_cap = 0;          // rows of the partial-sum buffer
+  float* f_Vin = nullptr;    // [(mi+1) n] inner FP32 Krylov basis
+  double* c_Vin = nullptr;   // [(mi+1) n] inner FP64 Krylov basis
+  double* hin = nullptr;     // device inner Hessenberg columns
+  double* hin_host = nullptr;
+};
+
+struct mf_ctx;
+struct MgLink {
+  mf_ctx* coarse = nullptr;      // next coarser level (caller-owned handle)
+  bool hcoarse = false;          // geometric (true) or polynomial coarsening
+  int32_t* parent = nullptr;     // [fine cells] coarse cell (h-coarsening)
+  uint8_t* child = nullptr;      // [fine cells] upper-half bits
+  double* inv_mult64 = nullptr;  // [fine nodes] 1 / number of cells sharing the node
+  float* inv_mult32 = nullptr;
+  XferTab tab;
 };
 
 struct ProfEvent {
@@ -78,10 +100,13 @@ struct mf_ctx {
   double *tau_r = nullptr, *tau_s = nullptr;
   int32_t* mc_cell = nullptr;
   double *mc_tau = nullptr, *mc_xi = nullptr, *mc_ang = nullptr, *mc_w = nullptr;
+  double* mg_jinv64 = nullptr;   // face geometry J^-1 at the mortar points [M][2][NP][d][d]
+  float* mg_jinv32 = nullptr;
   double *ht = nullptr, *g = nullptr;
   double* cache64 = nullptr;
   float* cache32 = nullptr;
   Workspace ws;
+  MgLink mg;
   std::string err;
 };
 
@@ -171,7 +196,8 @@ static void launch_jac(mf_ctx* h, const T* cache, const T* x, T* y, cudaStream_t
 template <int D, int K, typename T>
 static void launch_mortar(mf_ctx* h, int mode, const T* src, T* dst, int zero_wall, cudaStream_t st) {
   MortarArgs<T> A;
-  A.cells = h->cells; A.x = h->x; A.mc_cell = h->mc_cell; A.mc_tau = h->mc_tau; A.mc_xi = h->mc_xi;
+  A.cells = h->cells; A.mc_cell = h->mc_cell; A.mc_tau = h->mc_tau; A.mc_xi = h->mc_xi;
+  A.jinv = std::is_same<T, double>::value ? (const T*)h->mg_jinv64 : (const T*)h->mg_jinv32;
   A.mc_ang = h->mc_ang; A.mc_w = h->mc_w; A.nm = h->nm; A.src = src; A.dst = dst; A.nu = (T)h->nu;
   A.dz = h->H / h->n_z; A.zero_wall = zero_wall;
   using C = MortarCfg<D, K>;
@@ -202,6 +228,13 @@ static void launch_map(mf_ctx* h, cudaStream_t st) {
   A.ifr = h->ifr; A.ifs = h->ifs; A.tau_r = h->tau_r; A.tau_s = h->tau_s; A.n_R = h->n_R; A.n_z = h->n_z;
   A.R = h->R; A.phi0 = h->phi0; A.theta = h->theta;
   k_mortar_map<K><<<nblk(h->nm, 128), 128, 0, st>>>(A);
+}
+
+template <int D, int K>
+static void launch_mortar_geom(mf_ctx* h, cudaStream_t st) {
+  const int64_t nt = h->nm * 2 * ipow(K + 1, D - 1);
+  k_mortar_geom<D, K><<<nblk(nt, 128), 128, 0, st>>>(h->cells, h->x, h->mc_cell, h->mc_xi, h->nm, h->mg_jinv64,
+                                                     h->mg_jinv32);
 }
 
 // ------------------------------------------------------------------ mesh
@@ -239,9 +272,10 @@ extern "C" void mf_mesh_free(mf_mesh* m) { delete m; }
 // ------------------------------------------------------------------ create
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.V, w.Z, w.w, w.r, w.dx, w.hcol, w.part, w.diag64, w.dinv64, w.dinv32, w.f_v, w.f_x, w.f_r,
-                  w.f_d, w.f_t, w.c_x, w.c_r, w.c_d, w.c_t};
+                  w.f_d, w.f_t, w.f_w, w.c_x, w.c_r, w.c_d, w.c_t, w.utrial, w.f_Vin, w.c_Vin, w.hin, w.ep, w.jep};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (w.pinned) cudaFreeHost(w.pinned);
+  if (w.hin_host) cudaFreeHost(w.hin_host);
   w = Workspace();
 }
 
@@ -250,7 +284,8 @@ extern "C" mf_status mf_destroy(mf_handle h) {
   for (auto& e : h->prof_ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
-                  h->mc_cell, h->mc_tau, h->mc_xi, h->mc_ang, h->mc_w, h->ht, h->g, h->cache64, h->cache32};
+                  h->mc_cell, h->mc_tau, h->mc_xi, h->mc_ang, h->mc_w, h->ht, h->g, h->cache64, h->cache32,
+                  h->mg_jinv64, h->mg_jinv32, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32};
   for (void* p : ptrs) if (p) cudaFree(p);
   free_ws(h->ws);
   delete h;
@@ -271,6 +306,7 @@ static mf_status apply_angle(mf_ctx* h, double theta, cudaStream_t st) {
     case 4: launch_map<4>(h, st); break;
     case 5: launch_map<5>(h, st); break;
   }
+  MF_DISPATCH(h->d, h->k, (launch_mortar_geom<D, K>(h, st)));
   CK(cudaGetLastError());
   return MF_OK;
 }
@@ -313,6 +349,8 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
     ALLOC2(h->tau_r, h->nif); ALLOC2(h->tau_s, h->nif);
     ALLOC2(h->mc_cell, h->nm * 2); ALLOC2(h->mc_tau, h->nm); ALLOC2(h->mc_xi, h->nm * 2 * (k + 1));
     ALLOC2(h->mc_ang, h->nm * (k + 1)); ALLOC2(h->mc_w, h->nm * (k + 1));
+    ALLOC2(h->mg_jinv64, h->nm * 2 * ipow(k + 1, m->d - 1) * m->d * m->d);
+    ALLOC2(h->mg_jinv32, h->nm * 2 * ipow(k + 1, m->d - 1) * m->d * m->d);
     ALLOC2(h->ht, nn * d); ALLOC2(h->cache64, (size_t)h->ncache * nc * npc); ALLOC2(h->cache32, (size_t)h->ncache * nc * npc);
   } while (0);
 #undef ALLOC2
@@ -475,3 +513,4 @@ extern "C" mf_status mf_profile_read(mf_handle h, mf_profile_t* out) {
 }
 
 #include "mf_solve.inc"
+#include "mf_mg.inc"

@@ -200,11 +200,84 @@ __global__ void k_penalty(const int32_t* __restrict__ cells, const double* __res
 }
 
 // ---------------------------------------------------------------------------
+// Face geometry at the mortar points (set-up, once per rotor angle): J^-1 of
+// each side's cell map at its face point, FP64 and an FP32 copy.
+// Layout [M][2][NP][D][D], point index p = ia + (k+1) * iz.
+template <int D, int K>
+__global__ void k_mortar_geom(const int32_t* __restrict__ cells, const double* __restrict__ x,
+                              const int32_t* __restrict__ mc_cell, const double* __restrict__ mc_xi, int64_t nm,
+                              double* __restrict__ jinv64, float* __restrict__ jinv32) {
+  constexpr int N = K + 1, NPC = ipow(N, D), NP = ipow(N, D - 1);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nm * 2 * NP) return;
+  const int p = (int)(t % NP);
+  const int s = (int)((t / NP) % 2);
+  const int64_t mc = t / (2 * NP);
+  const MfTab<double>& tb = c_tab64[K];
+  const int ia = p % N, iz = (D == 3) ? p / N : 0;
+  double L0[N], dL0[N], L1[N], dL1[N];
+  lagrange_at<N, double>(tb, s == 0 ? 1.0 : 0.0, L0, dL0);
+  lagrange_at<N, double>(tb, mc_xi[(mc * 2 + s) * N + ia], L1, dL1);
+  const int64_t cell = mc_cell[2 * mc + s];
+  double J[D][D];
+#pragma unroll
+  for (int m = 0; m < D; ++m)
+#pragma unroll
+    for (int r = 0; r < D; ++r) J[m][r] = 0.0;
+  for (int b = 0; b < NPC; ++b) {
+    const int b0 = b % N, b1 = (b / N) % N, b2 = b / (N * N);
+    const double l2 = (D == 3) ? tb.B[iz][b2] : 1.0, d2 = (D == 3) ? tb.Dn[iz][b2] : 0.0;
+    const double dphi[3] = {dL0[b0] * L1[b1] * l2, L0[b0] * dL1[b1] * l2, L0[b0] * L1[b1] * d2};
+    int id = cells[cell * NPC + b];
+    id = id < 0 ? ~id : id;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      const double xm = x[(int64_t)id * D + m];
+#pragma unroll
+      for (int r = 0; r < D; ++r) J[m][r] = fma(dphi[r], xm, J[m][r]);
+    }
+  }
+  double Ji[D][D];
+  if (D == 2) {
+    const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det; Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+  } else {
+    double c[3][3];
+    c[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    c[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    c[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    c[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    c[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    c[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    c[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    c[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    c[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double det = J[0][0] * c[0][0] + J[0][1] * c[0][1] + J[0][2] * c[0][2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) Ji[r][m] = c[m][r] / det;
+  }
+#pragma unroll
+  for (int r = 0; r < D; ++r)
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      jinv64[t * D * D + r * D + m] = Ji[r][m];
+      jinv32[t * D * D + r * D + m] = (float)Ji[r][m];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Face terms.  MODE 0: dst += M src (Jacobian / residual, linear in src);
 // MODE 1: diag += diagonal of the face operator.  Per mortar cell and side s
 // (own = s, other = 1-s; jump = own - other; n_s own outward normal):
 //   -(q, 1/2 [[u]].n) + (v, {p} n) - (grad v : nu/2 [[u]] (x) n)
 //   - (v, nu {grad u} n) + (v, nu tau [[u]])
+// Traces by sum factorisation: the face-normal direction xi_0 is contracted
+// first (value = face layer of the nodes since l_b(face) is a Kronecker delta;
+// normal derivative with l_b'(face)), then the face directions with the 1D
+// tables at the point's angular coordinate and the Gauss z-points.  The test
+// side is integrated the same way in reverse.
 template <int D, int K> struct MortarCfg {
   static constexpr int N = K + 1, NPC = ipow(N, D), NP = ipow(N, D - 1);
   static constexpr int MPB = (2 * NPC >= 128) ? 1 : (256 / (2 * NPC));
@@ -212,8 +285,9 @@ template <int D, int K> struct MortarCfg {
 };
 
 template <typename T> struct MortarArgs {
-  const int32_t* cells; const double* x;
+  const int32_t* cells;
   const int32_t* mc_cell; const double* mc_tau; const double* mc_xi; const double* mc_ang; const double* mc_w;
+  const T* jinv;      // [M][2][NP][D][D]
   int64_t nm;
   const T* src; T* dst;
   T nu; double dz; int zero_wall;
@@ -223,115 +297,104 @@ template <int D, int K, typename T, int MODE>
 __global__ void __launch_bounds__(MortarCfg<D, K>::THREADS) k_mortar(MortarArgs<T> A) {
   using C = MortarCfg<D, K>;
   constexpr int N = C::N, NPC = C::NPC, NP = C::NP, NF = D + 1, MPB = C::MPB;
-  __shared__ T s_val[MPB][2][NPC][NF];
-  __shared__ T s_X[MPB][2][NPC][D];
-  __shared__ T s_U[MPB][2][NP][NF];
-  __shared__ T s_GU[MPB][2][NP][D][D];
-  __shared__ T s_Ji[MPB][2][NP][D][D];
-  __shared__ T s_L1[MPB][2][N][N];
+  __shared__ T s_val[MPB][2][NPC][NF];     // gathered nodal values
+  __shared__ T s_fa[MPB][2][NP][NF];       // face-layer values (b1,b2)
+  __shared__ T s_fn[MPB][2][NP][NF];       // normal derivative per (b1,b2)
+  __shared__ T s_U[MPB][2][NP][NF];        // traces at the points
+  __shared__ T s_GU[MPB][2][NP][D][D];     // physical velocity gradients at the points
+  __shared__ T s_L1[MPB][2][N][N];         // l_b(xi1 of angular point ia)  [ia][b]
   __shared__ T s_dL1[MPB][2][N][N];
-  __shared__ T s_fv[MPB][2][NP][NF];
-  __shared__ T s_Fx[MPB][2][NP][D][D];
+  __shared__ T s_fv[MPB][2][NP][NF];       // value fluxes
+  __shared__ T s_Fx[MPB][2][NP][D][D];     // reference gradient fluxes of v
+  __shared__ T s_G[MPB][2][NP][NF];        // integrated against face-layer test functions
+  __shared__ T s_H[MPB][2][NP][D];         // integrated against normal derivatives
   const MfTab<T>& tb = TabSel<T>::get(K);
   const int lm = threadIdx.x / (2 * NPC);
   const int loc = threadIdx.x % (2 * NPC);
   const int s = loc / NPC, a = loc % NPC;
   const int64_t mc = (int64_t)blockIdx.x * MPB + lm;
   const bool active = mc < A.nm;
-  // ---- phase 1: gather the two cells
+  const int fc = (s == 0) ? K : 0;         // index of the face layer along xi_0
+  T L0[N], dL0[N];
+  lagrange_at<N, T>(tb, (s == 0) ? T(1) : T(0), L0, dL0);
+  // ---- phase 1: gather, and 1D tables along the face
   int node = 0;
-  {
-    const int cell = active ? A.mc_cell[2 * mc + s] : 0;
-    if (active) {
-      const int id = A.cells[(int64_t)cell * NPC + a];
-      const bool wall = id < 0;
-      node = wall ? ~id : id;
+  if (active) {
+    const int cell = A.mc_cell[2 * mc + s];
+    const int id = A.cells[(int64_t)cell * NPC + a];
+    const bool wall = id < 0;
+    node = wall ? ~id : id;
+    if (MODE == 0) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) s_val[lm][s][a][f] = (MODE == 0) ? A.src[(int64_t)node * NF + f] : T(0);
-      if (MODE == 0 && wall && A.zero_wall) {
+      for (int f = 0; f < NF; ++f) s_val[lm][s][a][f] = A.src[(int64_t)node * NF + f];
+      if (wall && A.zero_wall) {
 #pragma unroll
         for (int c = 0; c < D; ++c) s_val[lm][s][a][c] = T(0);
       }
+    }
+    if (a < N) {
+      T L1[N], dL1[N];
+      lagrange_at<N, T>(tb, (T)A.mc_xi[(mc * 2 + s) * N + a], L1, dL1);
 #pragma unroll
-      for (int m = 0; m < D; ++m) s_X[lm][s][a][m] = (T)A.x[(int64_t)node * D + m];
-    } else {
+      for (int b = 0; b < N; ++b) { s_L1[lm][s][a][b] = L1[b]; s_dL1[lm][s][a][b] = dL1[b]; }
+    }
+  } else {
+    if (MODE == 0) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) s_val[lm][s][a][f] = T(0);
-      const int ai[3] = {a % N, (a / N) % N, a / (N * N)};
+    }
+    if (a < N) {
 #pragma unroll
-      for (int m = 0; m < D; ++m) s_X[lm][s][a][m] = (T)ai[m];
+      for (int b = 0; b < N; ++b) { s_L1[lm][s][a][b] = T(0); s_dL1[lm][s][a][b] = T(0); }
     }
   }
   __syncthreads();
-  // ---- phase 2: traces at the points of side s
-  const T xi0 = (s == 0) ? T(1) : T(0);
-  T L0[N], dL0[N];
-  lagrange_at<N, T>(tb, xi0, L0, dL0);
-  if (a < NP) {
-    const int p = a, ia = p % N, iz = (D == 3) ? p / N : 0;
-    const T xi1 = active ? (T)A.mc_xi[(mc * 2 + s) * N + ia] : T(0.5);
-    T L1[N], dL1[N];
-    lagrange_at<N, T>(tb, xi1, L1, dL1);
-    if (iz == 0) {
-#pragma unroll
-      for (int b = 0; b < N; ++b) { s_L1[lm][s][ia][b] = L1[b]; s_dL1[lm][s][ia][b] = dL1[b]; }
-    }
-    T u[NF], du[NF][D], J[D][D];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) { u[f] = T(0);
-#pragma unroll
-      for (int r = 0; r < D; ++r) du[f][r] = T(0); }
-#pragma unroll
-    for (int m = 0; m < D; ++m)
-#pragma unroll
-      for (int r = 0; r < D; ++r) J[m][r] = T(0);
-#pragma unroll
-    for (int b = 0; b < NPC; ++b) {
-      const int b0 = b % N, b1 = (b / N) % N, b2 = b / (N * N);
-      const T l2 = (D == 3) ? tb.B[iz][b2] : T(1);
-      const T d2 = (D == 3) ? tb.Dn[iz][b2] : T(0);
-      const T phi = L0[b0] * L1[b1] * l2;
-      T dphi[3] = {dL0[b0] * L1[b1] * l2, L0[b0] * dL1[b1] * l2, L0[b0] * L1[b1] * d2};
+  const T tau_f = active ? (T)A.mc_tau[mc] : T(0);
+  if (MODE == 0) {
+    // ---- phase 2a: contract xi_0 -> face layer and normal derivative, per (b1, b2) = q
+    if (a < NP) {
+      const int q = a;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        const T vv = s_val[lm][s][b][f];
-        u[f] = fma(phi, vv, u[f]);
+        T dn = T(0);
 #pragma unroll
-        for (int r = 0; r < D; ++r) du[f][r] = fma(dphi[r], vv, du[f][r]);
+        for (int b0 = 0; b0 < N; ++b0) dn = fma(dL0[b0], s_val[lm][s][b0 + N * q][f], dn);
+        s_fn[lm][s][q][f] = dn;
+        s_fa[lm][s][q][f] = s_val[lm][s][fc + N * q][f];
+      }
+    }
+    __syncthreads();
+    // ---- phase 2b: traces at point p = ia + N iz
+    if (a < NP) {
+      const int p = a, ia = p % N, iz = (D == 3) ? p / N : 0;
+      T u[NF], du[NF][D];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        u[f] = T(0);
+#pragma unroll
+        for (int r = 0; r < D; ++r) du[f][r] = T(0);
       }
 #pragma unroll
-      for (int m = 0; m < D; ++m)
+      for (int q = 0; q < NP; ++q) {
+        const int b1 = q % N, b2 = (D == 3) ? q / N : 0;
+        const T l1 = s_L1[lm][s][ia][b1], d1 = s_dL1[lm][s][ia][b1];
+        const T l2 = (D == 3) ? tb.B[iz][b2] : T(1), d2 = (D == 3) ? tb.Dn[iz][b2] : T(0);
+        const T w0 = l1 * l2, w1 = d1 * l2, w2 = l1 * d2;
 #pragma unroll
-        for (int r = 0; r < D; ++r) J[m][r] = fma(dphi[r], s_X[lm][s][b][m], J[m][r]);
-    }
-    T Ji[D][D];
-    if (D == 2) {
-      const T det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-      const T id = T(1) / det;
-      Ji[0][0] = J[1][1] * id; Ji[0][1] = -J[0][1] * id; Ji[1][0] = -J[1][0] * id; Ji[1][1] = J[0][0] * id;
-    } else {
-      T c[3][3];
-      c[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-      c[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-      c[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-      c[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-      c[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-      c[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-      c[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-      c[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-      c[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-      const T det = J[0][0] * c[0][0] + J[0][1] * c[0][1] + J[0][2] * c[0][2];
-      const T id = T(1) / det;
+        for (int f = 0; f < NF; ++f) {
+          const T fa = s_fa[lm][s][q][f];
+          u[f] = fma(w0, fa, u[f]);
+          du[f][0] = fma(w0, s_fn[lm][s][q][f], du[f][0]);
+          du[f][1] = fma(w1, fa, du[f][1]);
+          if (D == 3) du[f][2] = fma(w2, fa, du[f][2]);
+        }
+      }
+      const T* Ji = A.jinv + ((mc * 2 + s) * NP + p) * D * D;
+      T J[D][D];
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
+      for (int r = 0; r < D; ++r)
 #pragma unroll
-        for (int m = 0; m < 3; ++m) Ji[r][m] = c[m][r] * id;
-    }
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int m = 0; m < D; ++m) s_Ji[lm][s][p][r][m] = Ji[r][m];
-    if (MODE == 0) {
+        for (int m = 0; m < D; ++m) J[r][m] = active ? Ji[r * D + m] : T(0);
 #pragma unroll
       for (int f = 0; f < NF; ++f) s_U[lm][s][p][f] = u[f];
 #pragma unroll
@@ -340,99 +403,123 @@ __global__ void __launch_bounds__(MortarCfg<D, K>::THREADS) k_mortar(MortarArgs<
         for (int m = 0; m < D; ++m) {
           T g = T(0);
 #pragma unroll
-          for (int r = 0; r < D; ++r) g = fma(du[c][r], Ji[r][m], g);
+          for (int r = 0; r < D; ++r) g = fma(du[c][r], J[r][m], g);
           s_GU[lm][s][p][c][m] = g;
         }
     }
-  }
-  __syncthreads();
-  // ---- phase 3: fluxes of side s at its points
-  const T tau_f = active ? (T)A.mc_tau[mc] : T(0);
-  if (MODE == 0 && a < NP) {
-    const int p = a, ia = p % N, iz = (D == 3) ? p / N : 0;
-    const int o = 1 - s;
-    const double ang = active ? A.mc_ang[mc * N + ia] : 0.0;
-    double wd = active ? A.mc_w[mc * N + ia] : 0.0;
-    if (D == 3) wd *= (double)TabSel<double>::get(K).w[iz] * A.dz;
-    const T w = (T)wd;
-    const T sg = (s == 0) ? T(1) : T(-1);
-    T n[3] = {sg * (T)cos(ang), sg * (T)sin(ang), T(0)};
-    T jump[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) jump[c] = s_U[lm][s][p][c] - s_U[lm][o][p][c];
-    const T pavg = T(0.5) * (s_U[lm][s][p][D] + s_U[lm][o][p][D]);
-    T jn = T(0);
-#pragma unroll
-    for (int c = 0; c < D; ++c) jn = fma(jump[c], n[c], jn);
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      T gn = T(0);
-#pragma unroll
-      for (int m = 0; m < D; ++m) gn = fma(T(0.5) * (s_GU[lm][s][p][c][m] + s_GU[lm][o][p][c][m]), n[m], gn);
-      s_fv[lm][s][p][c] = w * (pavg * n[c] - A.nu * gn + A.nu * tau_f * jump[c]);
-    }
-    s_fv[lm][s][p][D] = -T(0.5) * w * jn;
-    // -nu/2 [[u]] (x) n in reference coordinates: Fx[c][r] = sum_m Ji[r][m] F[c][m]
-    T jin[D];
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      T t = T(0);
-#pragma unroll
-      for (int m = 0; m < D; ++m) t = fma(s_Ji[lm][s][p][r][m], n[m], t);
-      jin[r] = t;
-    }
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-#pragma unroll
-      for (int r = 0; r < D; ++r) s_Fx[lm][s][p][c][r] = -T(0.5) * w * A.nu * jump[c] * jin[r];
-  }
-  __syncthreads();
-  // ---- phase 4: integrate against the test functions of node a on side s
-  if (!active) return;
-  const int a0 = a % N, a1 = (a / N) % N, a2 = a / (N * N);
-  T out[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) out[f] = T(0);
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    const int ia = p % N, iz = (D == 3) ? p / N : 0;
-    const T l2 = (D == 3) ? tb.B[iz][a2] : T(1);
-    const T d2 = (D == 3) ? tb.Dn[iz][a2] : T(0);
-    const T l1 = s_L1[lm][s][ia][a1], dl1 = s_dL1[lm][s][ia][a1];
-    const T phi = L0[a0] * l1 * l2;
-    const T dphi[3] = {dL0[a0] * l1 * l2, L0[a0] * dl1 * l2, L0[a0] * l1 * d2};
-    if (MODE == 0) {
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        T acc = phi * s_fv[lm][s][p][c];
-#pragma unroll
-        for (int r = 0; r < D; ++r) acc = fma(dphi[r], s_Fx[lm][s][p][c][r], acc);
-        out[c] += acc;
-      }
-      out[D] = fma(phi, s_fv[lm][s][p][D], out[D]);
-    } else {
-      // diagonal: w [ -nu phi (grad phi . n_s) + nu tau phi^2 ] for each velocity component
-      const double ang = A.mc_ang[mc * N + ia];
-      double wd = A.mc_w[mc * N + ia];
-      if (D == 3) wd *= (double)TabSel<double>::get(K).w[iz] * A.dz;
+    __syncthreads();
+    // ---- phase 3: fluxes of side s at its points
+    if (a < NP) {
+      const int p = a, ia = p % N, iz = (D == 3) ? p / N : 0;
+      const int o = 1 - s;
+      const double ang = active ? A.mc_ang[mc * N + ia] : 0.0;
+      double wd = active ? A.mc_w[mc * N + ia] : 0.0;
+      if (D == 3) wd *= TabSel<double>::get(K).w[iz] * A.dz;
       const T w = (T)wd;
       const T sg = (s == 0) ? T(1) : T(-1);
       const T n[3] = {sg * (T)cos(ang), sg * (T)sin(ang), T(0)};
+      T jump[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) jump[c] = s_U[lm][s][p][c] - s_U[lm][o][p][c];
+      const T pavg = T(0.5) * (s_U[lm][s][p][D] + s_U[lm][o][p][D]);
+      T jn = T(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) jn = fma(jump[c], n[c], jn);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        T gn = T(0);
+#pragma unroll
+        for (int m = 0; m < D; ++m) gn = fma(s_GU[lm][s][p][c][m] + s_GU[lm][o][p][c][m], n[m], gn);
+        s_fv[lm][s][p][c] = w * (pavg * n[c] - T(0.5) * A.nu * gn + A.nu * tau_f * jump[c]);
+      }
+      s_fv[lm][s][p][D] = -T(0.5) * w * jn;
+      const T* Ji = A.jinv + ((mc * 2 + s) * NP + p) * D * D;
+      T jin[D];
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        T t = T(0);
+#pragma unroll
+        for (int m = 0; m < D; ++m) t = fma(active ? Ji[r * D + m] : T(0), n[m], t);
+        jin[r] = t;
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int r = 0; r < D; ++r) s_Fx[lm][s][p][c][r] = -T(0.5) * w * A.nu * jump[c] * jin[r];
+    }
+    __syncthreads();
+    // ---- phase 4a: integrate over the points per face position q = (a1, a2)
+    if (a < NP) {
+      const int q = a, a1 = q % N, a2 = (D == 3) ? q / N : 0;
+      T G[NF], Hn[D];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) G[f] = T(0);
+#pragma unroll
+      for (int c = 0; c < D; ++c) Hn[c] = T(0);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const int ia = p % N, iz = (D == 3) ? p / N : 0;
+        const T l1 = s_L1[lm][s][ia][a1], d1 = s_dL1[lm][s][ia][a1];
+        const T l2 = (D == 3) ? tb.B[iz][a2] : T(1), d2 = (D == 3) ? tb.Dn[iz][a2] : T(0);
+        const T w0 = l1 * l2, w1 = d1 * l2, w2 = l1 * d2;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          T acc = fma(w0, s_fv[lm][s][p][c], G[c]);
+          acc = fma(w1, s_Fx[lm][s][p][c][1], acc);
+          if (D == 3) acc = fma(w2, s_Fx[lm][s][p][c][D - 1], acc);
+          G[c] = acc;
+          Hn[c] = fma(w0, s_Fx[lm][s][p][c][0], Hn[c]);
+        }
+        G[D] = fma(w0, s_fv[lm][s][p][D], G[D]);
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) s_G[lm][s][q][f] = G[f];
+#pragma unroll
+      for (int c = 0; c < D; ++c) s_H[lm][s][q][c] = Hn[c];
+    }
+    __syncthreads();
+    if (!active) return;
+    // ---- phase 4b: node a = a0 + N q: out = l_a0(face) G_q + l'_a0(face) H_q
+    const int a0 = a % N, q = a / N;
+    T out[NF];
+#pragma unroll
+    for (int c = 0; c < D; ++c) out[c] = fma(L0[a0], s_G[lm][s][q][c], dL0[a0] * s_H[lm][s][q][c]);
+    out[D] = L0[a0] * s_G[lm][s][q][D];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) atomicAdd(&A.dst[(int64_t)node * NF + f], out[f]);
+  } else {
+    // ---- diagonal: w nu [tau phi^2 - phi (grad phi . n_s)] on face nodes, per velocity component
+    if (!active) return;
+    const int a0 = a % N, a1 = (a / N) % N, a2 = a / (N * N);
+    if (a0 != fc) return;
+    T dv = T(0);
+    const T sg = (s == 0) ? T(1) : T(-1);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int ia = p % N, iz = (D == 3) ? p / N : 0;
+      const double ang = A.mc_ang[mc * N + ia];
+      double wd = A.mc_w[mc * N + ia];
+      if (D == 3) wd *= TabSel<double>::get(K).w[iz] * A.dz;
+      const T w = (T)wd;
+      const T n[3] = {sg * (T)cos(ang), sg * (T)sin(ang), T(0)};
+      const T l1 = s_L1[lm][s][ia][a1], d1 = s_dL1[lm][s][ia][a1];
+      const T l2 = (D == 3) ? tb.B[iz][a2] : T(1), d2 = (D == 3) ? tb.Dn[iz][a2] : T(0);
+      const T phi = l1 * l2;
+      const T dphi[3] = {dL0[a0] * l1 * l2, d1 * l2, l1 * d2};
+      const T* Ji = A.jinv + ((mc * 2 + s) * NP + p) * D * D;
       T gn = T(0);
 #pragma unroll
       for (int m = 0; m < D; ++m) {
         T g = T(0);
 #pragma unroll
-        for (int r = 0; r < D; ++r) g = fma(dphi[r], s_Ji[lm][s][p][r][m], g);
+        for (int r = 0; r < D; ++r) g = fma(dphi[r], Ji[r * D + m], g);
         gn = fma(g, n[m], gn);
       }
-      const T dv = w * A.nu * (tau_f * phi * phi - phi * gn);
-#pragma unroll
-      for (int c = 0; c < D; ++c) out[c] += dv;
+      dv += w * A.nu * (tau_f * phi * phi - phi * gn);
     }
-  }
 #pragma unroll
-  for (int f = 0; f < NF; ++f) atomicAdd(&A.dst[(int64_t)node * NF + f], out[f]);
+    for (int c = 0; c < D; ++c) atomicAdd(&A.dst[(int64_t)node * NF + c], dv);
+  }
 }
 
 }  // namespace mf

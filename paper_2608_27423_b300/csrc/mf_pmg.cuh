@@ -1,0 +1,111 @@
+// Multigrid transfers between a fine level and a coarser level of the global-
+// coarsening multigrid (Section 3.4): polynomial coarsening (same cells,
+// degree KC < KF) or geometric coarsening (each coarse cell split into 2^d
+// fine cells; parent[c] and child[c] bit r = upper half along xi_r).
+// In the parent's reference coordinates a fine node at xi_f sits at
+//   s(xi_f) = xi_f (p), xi_f / 2 (lower half), (1 + xi_f) / 2 (upper half).
+//   prolongation  u_f(a) = sum_b prod_r l^KC_{b_r}(s_r(x^KF_{a_r})) u_c(b)
+//   restriction   r_c(b) += sum_a [same weights] r_f(a) / mult(a)   (transpose)
+//   state interpolation u_c(b) = fine field at the coarse node, evaluated in
+//                 the fine cell that contains it
+// mult(a) = number of fine cells sharing node a.  Prolongation and
+// interpolation write node values (continuous fields: every cell writes the
+// same value); restriction accumulates.
+#pragma once
+#include "mf_cell.cuh"
+
+namespace mf {
+
+struct XferTab {
+  double icf[3][MF_NMAX][MF_NMAX];   // [code][fine node a][coarse node b]
+  double ifc[3][MF_NMAX][MF_NMAX];   // [code][coarse node b][fine node a]
+  unsigned char in_child[3][MF_NMAX];  // coarse node b lies in the child's half (code 1, 2) or always (code 0)
+};
+
+template <int D, int KF, int KC, int NFLD, int MODE, typename T>
+__global__ void k_transfer(const int32_t* __restrict__ cells_f, const int32_t* __restrict__ cells_c,
+                           const int32_t* __restrict__ parent, const uint8_t* __restrict__ child, int64_t ncf,
+                           const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ inv_mult,
+                           int in_stride, int out_stride, const XferTab tb) {
+  constexpr int NFN = KF + 1, NCN = KC + 1;
+  constexpr int NPF = ipow(NFN, D), NPC = ipow(NCN, D);
+  constexpr int NIN = (MODE == 1) ? NPC : NPF;
+  constexpr int NOUT = (MODE == 1) ? NPF : NPC;
+  constexpr int CPB = 4;
+  __shared__ T s_in[CPB][NIN][NFLD];
+  const int cl = threadIdx.y;
+  const int64_t cell = (int64_t)blockIdx.x * CPB + cl;
+  const bool active = cell < ncf;
+  const int64_t pcell = active ? (parent ? (int64_t)parent[cell] : cell) : 0;
+  int code[3] = {0, 0, 0};
+  if (active && parent) {
+    const int bits = child[cell];
+#pragma unroll
+    for (int r = 0; r < D; ++r) code[r] = 1 + ((bits >> r) & 1);
+  }
+  for (int i = threadIdx.x; i < NIN; i += blockDim.x) {
+    if (active) {
+      int id = (MODE == 1) ? cells_c[pcell * NPC + i] : cells_f[cell * NPF + i];
+      id = id < 0 ? ~id : id;
+      const T sc = (MODE == 2) ? inv_mult[id] : T(1);
+#pragma unroll
+      for (int f = 0; f < NFLD; ++f) s_in[cl][i][f] = in[(int64_t)id * in_stride + f] * sc;
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  for (int o = threadIdx.x; o < NOUT; o += blockDim.x) {
+    constexpr int nout = (MODE == 1) ? NFN : NCN, nin = (MODE == 1) ? NCN : NFN;
+    const int oi[3] = {o % nout, (o / nout) % nout, o / (nout * nout)};
+    if (MODE == 0) {
+      bool inside = true;
+#pragma unroll
+      for (int r = 0; r < D; ++r) inside = inside && tb.in_child[code[r]][oi[r]];
+      if (!inside) continue;
+    }
+    T acc[NFLD];
+#pragma unroll
+    for (int f = 0; f < NFLD; ++f) acc[f] = T(0);
+    for (int i = 0; i < NIN; ++i) {
+      const int ii[3] = {i % nin, (i / nin) % nin, i / (nin * nin)};
+      double w = 1.0;
+#pragma unroll
+      for (int r = 0; r < D; ++r) {
+        if (MODE == 0) w *= tb.ifc[code[r]][oi[r]][ii[r]];
+        else if (MODE == 1) w *= tb.icf[code[r]][oi[r]][ii[r]];
+        else w *= tb.icf[code[r]][ii[r]][oi[r]];
+      }
+#pragma unroll
+      for (int f = 0; f < NFLD; ++f) acc[f] = fma((T)w, s_in[cl][i][f], acc[f]);
+    }
+    int id = (MODE == 1) ? cells_f[cell * NPF + o] : cells_c[pcell * NPC + o];
+    id = id < 0 ? ~id : id;
+#pragma unroll
+    for (int f = 0; f < NFLD; ++f) {
+      if (MODE == 2) atomicAdd(&out[(int64_t)id * out_stride + f], acc[f]);
+      else out[(int64_t)id * out_stride + f] = acc[f];
+    }
+  }
+}
+
+// number of cells sharing each node (as T), then its reciprocal
+template <typename T>
+__global__ void k_count_nodes(const int32_t* __restrict__ cells, int64_t n, T* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int id = cells[i];
+  id = id < 0 ? ~id : id;
+  atomicAdd(&cnt[id], T(1));
+}
+
+// zero the velocity components of wall rows
+template <int D, typename T>
+__global__ void k_dirichlet_zero(const int32_t* __restrict__ wall, int64_t nw, T* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nw) return;
+  const int64_t n = wall[i];
+#pragma unroll
+  for (int c = 0; c < D; ++c) y[n * (D + 1) + c] = T(0);
+}
+
+}  // namespace mf

@@ -143,9 +143,12 @@ __global__ void k_axpby(int64_t n, T a, const T* __restrict__ x, T b, T* __restr
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
 }
-// y = x * s / *scal  (scal read on the device: no host round trip)
-__global__ void k_scale_by(int64_t n, const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ nrm2) {
-  const double inv = 1.0 / sqrt(*nrm2);
+// y = x / sqrt(*nrm2)  (norm read on the device: no host round trip); a zero
+// norm gives y = 0 instead of a division by zero.
+template <typename T>
+__global__ void k_scale_by(int64_t n, const T* __restrict__ x, T* __restrict__ y, const double* __restrict__ nrm2) {
+  const double nn = *nrm2;
+  const T inv = nn > 1e-300 ? (T)(1.0 / sqrt(nn)) : T(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = x[i] * inv;
 }
@@ -162,13 +165,17 @@ __global__ void k_recip(int64_t n, const T* __restrict__ a, T* __restrict__ y) {
 
 // Partial dot products: part[i][blockIdx.x] = sum over the block's range of V_i . w
 // (V_i = V + i * ldv), one grid row per vector (blockIdx.y = i).
-__global__ void k_mdot_part(int64_t n, const double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
+// Thread-level accumulation in T (FP32 vectors accumulate a few dozen terms per
+// thread in FP32), block and final reductions in FP64.
+template <typename T>
+__global__ void k_mdot_part(int64_t n, const T* __restrict__ V, int64_t ldv, const T* __restrict__ w,
                             double* __restrict__ part) {
   const int i = blockIdx.y;
-  const double* v = V + (int64_t)i * ldv;
-  double s = 0.0;
+  const T* v = V + (int64_t)i * ldv;
+  T st = T(0);
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    s = fma(v[j], w[j], s);
+    st = fma(v[j], w[j], st);
+  double s = (double)st;
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -194,12 +201,13 @@ __global__ void k_mdot_final(const double* __restrict__ part, int nb, double* __
     if (threadIdx.x == 0) out[i] = accumulate ? out[i] + s : s;
   }
 }
-// w -= sum_{i<m} h[i] V_i   (sign = -1) or w += (sign = +1)
-__global__ void k_maxpy(int64_t n, int m, const double* __restrict__ V, int64_t ldv, const double* __restrict__ h,
-                        double sign, double* __restrict__ w) {
+// w += sign * sum_{i<m} h[i] V_i  (h in FP64 on the device)
+template <typename T>
+__global__ void k_maxpy(int64_t n, int m, const T* __restrict__ V, int64_t ldv, const double* __restrict__ h,
+                        double sign, T* __restrict__ w) {
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    double s = w[j];
-    for (int i = 0; i < m; ++i) s = fma(sign * __ldg(h + i), V[(int64_t)i * ldv + j], s);
+    T s = w[j];
+    for (int i = 0; i < m; ++i) s = fma((T)(sign * __ldg(h + i)), V[(int64_t)i * ldv + j], s);
     w[j] = s;
   }
 }

@@ -3,13 +3,14 @@
 * ``2d_q2``: 2D disk r<0.5 (O-grid m=16, 5 rings: 576 quads) in an annulus
   0.5<r<1 (64 x 12 = 768 quads), interface rotated by 0.137 rad (non-matching),
   Q2, nu=0.01, omega=1, BDF1, dt=0.01; i.i.d. U(-1,1) state.
-* ``3d_q2``: cylinder R_out=1, H=1, rotor r<0.5: m=28, n_r=9, n_s=18, n_z=36
-  -> 137,088 hexes, Q2 (4.55M DoFs); Re = omega D^2/(2 pi nu) = 200 with D=1,
-  omega=1; BDF2, dt=0.005; smooth low-mode state.
-* ``3d_q3``: same cylinder, m=22, n_r=7, n_s=14, n_z=25 -> 58,300 hexes, Q3
-  (6.5M DoFs); Re = 200.
-* ``3d_q2_mid``: the 3d_q2 physics on m=12, n_r=4, n_s=8, n_z=36 (25,920 hexes,
-  0.86M DoFs; per-point cache 196 MB, still larger than L2) for profiling.
+* ``3d_q2``: cylinder R_out=1, H=1, rotor r<0.5: m=32, n_r=8, n_s=16, n_z=32
+  -> 131,072 hexes, Q2 (4.36M DoFs); Re = omega D^2/(2 pi nu) = 200 with D=1,
+  omega=1; BDF2, dt=0.005; smooth low-mode state.  Coarsens uniformly three
+  times (h-multigrid).
+* ``3d_q3``: same cylinder, m=24, n_r=8, n_s=12, n_z=24 -> 59,904 hexes, Q3
+  (6.69M DoFs); Re = 200.
+* ``3d_q2_mid``: the 3d_q2 physics on m=16, n_r=4, n_s=8, n_z=16 (16,384 hexes,
+  0.56M DoFs; per-point cache 124 MB) for profiling and solver checks.
 * small variants for tests.
 """
 import numpy as np
@@ -20,11 +21,11 @@ SEED = 20260
 CONFIGS = {
     "2d_q2": dict(d=2, k=2, m=16, n_r=5, n_s=12, n_z=1, nu=0.01, omega=1.0, dt=0.01, bdf=1,
                   theta=0.137, state="iid"),
-    "3d_q2": dict(d=3, k=2, m=28, n_r=9, n_s=18, n_z=36, nu=1.0 / (400.0 * np.pi), omega=1.0,
+    "3d_q2": dict(d=3, k=2, m=32, n_r=8, n_s=16, n_z=32, nu=1.0 / (400.0 * np.pi), omega=1.0,
                   dt=0.005, bdf=2, theta=0.137, state="smooth"),
-    "3d_q2_mid": dict(d=3, k=2, m=12, n_r=4, n_s=8, n_z=36, nu=1.0 / (400.0 * np.pi), omega=1.0,
+    "3d_q2_mid": dict(d=3, k=2, m=16, n_r=4, n_s=8, n_z=16, nu=1.0 / (400.0 * np.pi), omega=1.0,
                       dt=0.005, bdf=2, theta=0.137, state="smooth"),
-    "3d_q3": dict(d=3, k=3, m=22, n_r=7, n_s=14, n_z=25, nu=1.0 / (400.0 * np.pi), omega=1.0,
+    "3d_q3": dict(d=3, k=3, m=24, n_r=8, n_s=12, n_z=24, nu=1.0 / (400.0 * np.pi), omega=1.0,
                   dt=0.005, bdf=2, theta=0.137, state="smooth"),
 }
 

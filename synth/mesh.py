@@ -208,3 +208,61 @@ def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55
                            node_side=node_side3, wall=wall3, iface_rotor=ifr3.astype(np.int32),
                            iface_stator=ifs3.astype(np.int32), R=R, n_R=n_R, n_z=n_z, H=H,
                            phi0=phi0, params=params)
+
+
+def coarsen(params):
+    """Parameters of the uniformly coarsened mesh (every block halved in each of
+    its cell directions) and the parent map of the fine cells.
+
+    Returns (coarse_params, parent [N_c fine] int32, child [N_c fine] uint8):
+    parent[c] is the coarse cell containing fine cell c, bit r of child[c] is 1
+    when c is the upper half of its parent along xi_r.  Requires m, n_r, n_s
+    (and n_z in 3D) even.  Both meshes use the same parametric block maps, so
+    the fine cells subdivide the coarse cells in parameter space.
+    """
+    d, m, n_r, n_s, n_z = params["d"], params["m"], params["n_r"], params["n_s"], params["n_z"]
+    if m % 2 or n_r % 2 or n_s % 2 or (d == 3 and n_z % 2):
+        raise ValueError("m, n_r, n_s (and n_z in 3D) must be even to coarsen")
+    cp = dict(params, m=m // 2, n_r=n_r // 2, n_s=n_s // 2, n_z=(n_z // 2 if d == 3 else n_z))
+    mc, n_R, n_Rc = m // 2, 4 * m, 2 * m
+    parent, child = [], []
+    # centre square (xi_0 = x, xi_1 = y), index cy*m + cx
+    for cy in range(m):
+        for cx in range(m):
+            parent.append((cy // 2) * mc + cx // 2)
+            child.append((cx % 2) | ((cy % 2) << 1))
+    nsq_c = mc * mc
+    # ring cells (xi_0 radial, xi_1 angular), index n_sq + jr*n_R + j
+    for jr in range(n_r):
+        for j in range(n_R):
+            parent.append(nsq_c + (jr // 2) * n_Rc + j // 2)
+            child.append((jr % 2) | ((j % 2) << 1))
+    nrot_c = nsq_c + (n_r // 2) * n_Rc
+    for jr in range(n_s):
+        for j in range(n_R):
+            parent.append(nrot_c + (jr // 2) * n_Rc + j // 2)
+            child.append((jr % 2) | ((j % 2) << 1))
+    parent = np.array(parent, dtype=np.int64)
+    child = np.array(child, dtype=np.uint8)
+    if d == 3:
+        nc2, nc2c = len(parent), nrot_c + (n_s // 2) * n_Rc
+        lz = np.arange(n_z)
+        parent = ((lz[:, None] // 2) * nc2c + parent[None, :]).ravel()
+        child = (child[None, :] | ((lz[:, None] % 2) << 2).astype(np.uint8)).ravel()
+    return cp, parent.astype(np.int32), child.astype(np.uint8)
+
+
+def hierarchy(params, levels):
+    """Meshes of an h-hierarchy: [(mesh, parent, child)] from fine to coarse;
+    parent/child of the coarsest level are None."""
+    out = []
+    p = dict(params)
+    for lev in range(levels):
+        mesh = rotor_stator_mesh(p["d"], p["k"], p["m"], p["n_r"], p["n_s"], p.get("n_z", 1))
+        if lev + 1 < levels:
+            cp, parent, child = coarsen(dict(p, n_z=p.get("n_z", 1)))
+            out.append((mesh, parent, child))
+            p = cp
+        else:
+            out.append((mesh, None, None))
+    return out
