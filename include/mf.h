@@ -189,6 +189,34 @@ void mf_solver_defaults(mf_solver_opts* o);
 mf_status mf_solve_step(mf_handle h, double* up, const mf_solver_opts* so, mf_solve_report* rep,
                         void* stream);
 
+/* ---------------------------------------------------------------- no-allocation solve
+ * mf_solve_step_static: the same Newton / FGMRES step as mf_solve_step, for
+ * callers that must not allocate device memory during the solve -- e.g. a
+ * serving process whose own allocator has reserved the device memory up front
+ * (a cudaMalloc from the library would fail or break its accounting), or a
+ * control loop that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation.  (The paper has no counterpart: this is a deployment
+ * variant of the solver's workspace handling.)
+ *
+ * The Krylov workspace lives in one file-scope device array of
+ * MF_STATIC_WS_DOUBLES doubles (32 MiB) that every GPU which loads libmf.so
+ * holds until the process exits.  The call allocates no device or pinned host
+ * memory: no cudaMalloc, cudaFree, cudaMallocHost or event creation.  Limits:
+ *   - pc must be MF_PC_JACOBI with pc_precision MF_FP64;
+ *   - (2*restart + 10) * n_dofs + 3*(restart + 2) + (restart + 2) * 592 doubles
+ *     must fit in the array, otherwise MF_ERR_ARG with a message (e.g. 2D
+ *     workloads of ~16k DoFs with restart <= 100);
+ *   - per-kernel profiling (mf_profile) must be off (MF_ERR_STATE otherwise).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the previous call's contents; the
+ * solve initialises everything it reads.  Calls that overlap on the GPU (two
+ * streams, two threads, two handles) race on the array: serialise them.
+ * Arguments, results and errors are those of mf_solve_step. */
+#define MF_STATIC_WS_DOUBLES (4u << 20)
+mf_status mf_solve_step_static(mf_handle h, double* up, const mf_solver_opts* so, mf_solve_report* rep,
+                               void* stream);
+
 /* ---------------------------------------------------------------- multigrid
  * The global-coarsening multigrid of Section 3.4 (geometric and polynomial
  * coarsening) as a hierarchy of operator handles.  mf_mg_attach links `coarse`

@@ -19,7 +19,7 @@ EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_create", "mf_destroy", "mf
            "mf_set_angle", "mf_node_coords", "mf_dirichlet", "mf_set_history", "mf_set_linearization",
            "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step",
            "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
-           "mf_mg_interpolate"]
+           "mf_mg_interpolate", "mf_solve_step_static"]
 PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
               "cell_linearization", "dirichlet", "diagonal"]
 
@@ -82,6 +82,7 @@ def load():
     lib.mf_solver_defaults.argtypes = [C.POINTER(MfSolverOpts)]
     lib.mf_solver_defaults.restype = None
     lib.mf_solve_step.argtypes = [vp, vp, C.POINTER(MfSolverOpts), C.POINTER(MfSolveReport), vp]
+    lib.mf_solve_step_static.argtypes = [vp, vp, C.POINTER(MfSolverOpts), C.POINTER(MfSolveReport), vp]
     lib.mf_mg_attach.argtypes = [vp, vp, vp, vp]
     lib.mf_mg_prolongate.argtypes = [vp, vp, vp, vp]
     lib.mf_mg_restrict.argtypes = [vp, vp, vp, vp]

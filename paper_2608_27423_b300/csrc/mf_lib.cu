@@ -514,3 +514,75 @@ extern "C" mf_status mf_profile_read(mf_handle h, mf_profile_t* out) {
 
 #include "mf_solve.inc"
 #include "mf_mg.inc"
+
+// ---------------------------------------------------------------- no-allocation solve
+// Workspace of mf_solve_step_static: a file-scope device array.  In host code
+// the name is only a host-side stand-in; kernels get the device address looked
+// up with cudaGetSymbolAddress (once per device, on the first call).
+static __device__ __align__(256) double mf_static_ws[MF_STATIC_WS_DOUBLES];
+static double* g_static_ws_dev[64] = {nullptr};
+static double g_static_host[3 * (200 + 2)];      // host staging for the small read-backs
+
+extern "C" mf_status mf_solve_step_static(mf_handle h, double* up, const mf_solver_opts* so_in, mf_solve_report* rep,
+                                          void* stream) {
+  if (!h || !up) return MF_ERR_ARG;
+  mf_solver_opts so;
+  if (so_in) so = *so_in; else mf_solver_defaults(&so);
+  if (so.pc != MF_PC_JACOBI || so.pc_precision != MF_FP64) {
+    h->err = "mf_solve_step_static: only pc = MF_PC_JACOBI with pc_precision = MF_FP64";
+    return MF_ERR_ARG;
+  }
+  if (h->prof) { h->err = "mf_solve_step_static: disable profiling (it creates events)"; return MF_ERR_STATE; }
+  const int m = std::min(std::max(so.restart, 1), 200);
+  const int64_t n = h->ndof;
+  const int part_cap = m + 2;
+  const int64_t need = (int64_t)(2 * m + 10) * n + 3 * (m + 2) + (int64_t)part_cap * h->nb;
+  if (need > (int64_t)MF_STATIC_WS_DOUBLES) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf),
+                  "mf_solve_step_static: needs %lld doubles for %lld DoFs with restart %d, the static workspace "
+                  "holds %u",
+                  (long long)need, (long long)n, m, (unsigned)MF_STATIC_WS_DOUBLES);
+    h->err = buf;
+    return MF_ERR_ARG;
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) { h->err = "mf_solve_step_static: device index out of range"; return MF_ERR_ARG; }
+  if (!g_static_ws_dev[dev]) {
+    double* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void**)&p, mf_static_ws);
+    if (e != cudaSuccess || !p) {
+      h->err = std::string("mf_solve_step_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return MF_ERR_CUDA;
+    }
+    g_static_ws_dev[dev] = p;
+  }
+  // carve the view: V (m+1)n, Z m n, then w r dx diag64 dinv64 utrial ep jep dinv32, hcol, part
+  double* p = g_static_ws_dev[dev];
+  Workspace view;
+  view.m = m;
+  view.V = p; p += (size_t)(m + 1) * n;
+  view.Z = p; p += (size_t)m * n;
+  view.w = p; p += n;
+  view.r = p; p += n;
+  view.dx = p; p += n;
+  view.diag64 = p; p += n;
+  view.dinv64 = p; p += n;
+  view.utrial = p; p += n;
+  view.ep = p; p += n;
+  view.jep = p; p += n;
+  view.dinv32 = (float*)p; p += n;      // n floats (half of this slot is spare)
+  view.hcol = p; p += 3 * (m + 2);
+  view.part = p; p += (size_t)part_cap * h->nb;
+  view.part_cap = part_cap;
+  view.pinned = g_static_host;
+  // the small scalars start at zero on every call
+  CK(cudaMemsetAsync(view.hcol, 0, sizeof(double) * (3 * (m + 2) + (size_t)part_cap * h->nb), S(stream)));
+  Workspace saved = h->ws;
+  h->ws = view;
+  so.restart = m;
+  const mf_status st = mf_solve_step(h, up, &so, rep, stream);
+  h->ws = saved;
+  return st;
+}
