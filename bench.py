@@ -26,6 +26,9 @@ sys.path.insert(0, ROOT)
 METRIC = "Jacobian-apply DoFs/s (FP64 vs FP32) at Q2/Q3; time to 1e-8 residual per step"
 FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (non-tensor) nominal
 FP64_PROBE_TFLOPS = 1.128        # FMA-chain probe on the B300s
+# DRAM bytes (read + write) per cell of k_cell_jac<3,2,double> from one ncu capture on the 16,384-hex
+# cylinder (profiles/k_cell_jac_fp64_3d_q2_mid.md: 134.845 MB + 4.531 MB); traffic scales with the cells.
+TRAFFIC_BYTES_PER_CELL_Q2_3D_FP64 = (134.844928e6 + 4.531456e6) / 16384
 
 
 def parse():
@@ -38,7 +41,9 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--max-newton", type=int, default=15)
+    ap.add_argument("--max-newton", type=int, default=20)
+    ap.add_argument("--mg-levels", type=int, default=4)
+    ap.add_argument("--batched", action="store_true", help="also time 12 uneven instances, batched vs one by one")
     return ap.parse_args()
 
 
@@ -109,10 +114,134 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
+import synth  # noqa: E402  (seeded input generator: meshes and fields)
+
+
 def build_inputs(workload):
-    import synth
     mesh, prm, f = synth.make_config(workload)
     return mesh, prm, f
+
+
+# --------------------------------------------------------------------- solve leg
+def build_levels(op, cfg, prm, n_h):
+    """Multigrid levels below `op`: one polynomial level (k -> k-1) when k >= 3,
+    then geometric halvings of the mesh (n_h levels in all below the finest)."""
+    from paper_2608_27423_b300 import RotorStatorOperator
+    base = dict(d=cfg["d"], k=cfg["k"], m=cfg["m"], n_r=cfg["n_r"], n_s=cfg["n_s"], n_z=cfg["n_z"])
+    levels = [op]
+    if cfg["k"] >= 3:
+        pm = synth.rotor_stator_mesh(cfg["d"], cfg["k"] - 1, cfg["m"], cfg["n_r"], cfg["n_s"], cfg["n_z"])
+        lp = RotorStatorOperator(pm, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
+        op.mg_attach(lp)
+        levels.append(lp)
+        base = dict(base, k=cfg["k"] - 1)
+    p = base
+    for _ in range(n_h):
+        try:
+            cp, parent, child = synth.mesh.coarsen(p)
+        except ValueError:
+            break
+        cm = synth.rotor_stator_mesh(cp["d"], cp["k"], cp["m"], cp["n_r"], cp["n_s"], cp["n_z"])
+        lc = RotorStatorOperator(cm, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
+        levels[-1].mg_attach(lc, parent, child)
+        levels.append(lc)
+        p = cp
+    return levels
+
+
+def solve_leg(args, op, mesh, prm, f, T):
+    """Newton + FGMRES(30) (FP64 residual, Jacobian applies and CGS2)
+    preconditioned by one V-cycle of the global-coarsening multigrid (GMRES-Jacobi
+    smoothing), with the V-cycle's operator applies in FP32 (mixed) or FP64.
+    Initial guess: u^n with p = 0 and zero wall velocity."""
+    import torch
+    from paper_2608_27423_b300 import MF_PC_MG, MF_FP32, MF_FP64, solver_defaults
+    from synth.configs import CONFIGS
+    d = mesh.d
+    cfg = CONFIGS[args.workload]
+    levels = build_levels(op, cfg, prm, args.mg_levels - 1)
+    u0 = np.zeros_like(f["up_star"])
+    u0[:, :d] = f["u_n"]
+    u0[mesh.wall.astype(bool), :d] = 0.0
+    U0 = T(u0)
+    res = {"levels": [f"Q{lv.k}:{lv.n_cells}" for lv in levels]}
+    sols = {}
+    for name, pcp in (("mixed_fp32_mg", MF_FP32), ("fp64_mg", MF_FP64)):
+        up = U0.clone()
+        o = solver_defaults(theta=prm["theta"], pc=MF_PC_MG, pc_precision=pcp, newton_rtol=1e-8,
+                            max_newton=args.max_newton, lin_rtol=1e-2, restart=30, max_lin_iters=150,
+                            mg_smooth=4, mg_coarse_iters=40)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, rep = op.solve_step(up, o)
+        torch.cuda.synchronize()
+        dt_s = time.perf_counter() - t0
+        n_it = rep.newton_iters
+        res[name] = {"status": int(st), "seconds": round(dt_s, 4), "newton_iters": n_it,
+                     "lin_iters": list(rep.lin_iters[:n_it]),
+                     "res_reduction": (rep.res_norm[n_it] / rep.res_norm[0]) if rep.res_norm[0] > 0 else None}
+        print(f"solve {name}: status {st} {dt_s:.2f}s newton {n_it} "
+              f"res {rep.res_norm[0]:.3e} -> {rep.res_norm[n_it]:.3e}", file=sys.stderr, flush=True)
+        sols[name] = up
+    a, b = sols["fp64_mg"], sols["mixed_fp32_mg"]
+    va, vb = a[:, :d], b[:, :d]
+    pa, pb = a[:, d] - a[:, d].mean(), b[:, d] - b[:, d].mean()
+    res["rel_velocity_diff_mixed_vs_fp64"] = float((va - vb).norm() / va.norm())
+    res["rel_pressure_diff_mixed_vs_fp64_mean_removed"] = float((pa - pb).norm() / pa.norm())
+    if res["mixed_fp32_mg"]["seconds"] > 0:
+        res["speedup_mixed_vs_fp64"] = res["fp64_mg"]["seconds"] / res["mixed_fp32_mg"]["seconds"]
+    return res
+
+
+# --------------------------------------------------------------------- batched sweep
+BATCH_RE = [1, 2, 5, 10, 20, 50, 100, 200, 500, 1000, 1500, 2000]
+
+
+def batched_leg(args, T, dev):
+    """12 independent cylinders (Re in BATCH_RE, omega = 1, Q2, BDF2 dt = 0.005,
+    rotor angle 0.137 i, m = 16 .. 32 -> ~16k .. ~131k hexes): FP64 Jacobian
+    applies of all instances, one persistent launch per kernel kind against
+    the instances applied one after another."""
+    import torch
+    from paper_2608_27423_b300 import RotorStatorOperator, BatchedOperators
+    ops, xs = [], []
+    for i, re in enumerate(BATCH_RE):
+        m = 16 + (16 * i) // 11
+        m -= m % 2
+        nu = 1.0 / (2.0 * np.pi * re)
+        mesh, prm, f = synth.make_config(d=3, k=2, m=m, n_r=max(2, m // 4), n_s=m // 2, n_z=m, nu=nu, omega=1.0,
+                                         dt=0.005, bdf=2, theta=0.137 * i, state="smooth", seed=20260 + 10 * i)
+        op = RotorStatorOperator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
+        op.set_history(T(f["u_n"]), T(f["u_nm1"]))
+        op.set_linearization(T(f["up_star"]), prm["theta"])
+        ops.append(op)
+        xs.append(T(f["x"]))
+    ys = [torch.empty_like(x) for x in xs]
+    batch = BatchedOperators(ops)
+    stream = torch.cuda.current_stream()
+    steps = max(10, args.steps // 5)
+
+    def run(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def seq():
+        for op, x, y in zip(ops, xs, ys):
+            op.apply_jacobian(x, y)
+    ms_seq = run(seq)
+    ms_bat = run(lambda: batch.apply_jacobian(xs, ys))
+    dofs = sum(op.n_dofs for op in ops)
+    return {"instances": len(ops), "cells": [op.n_cells for op in ops], "total_dofs": dofs,
+            "ms_one_by_one": ms_seq, "ms_batched": ms_bat, "dofs_per_s_batched": dofs / (ms_bat * 1e-3),
+            "speedup": ms_seq / ms_bat}
 
 
 # --------------------------------------------------------------------- CPU oracle
@@ -246,8 +375,9 @@ def main():
     ncache = (d * d + 1 + d * (d + 1) // 2 + d + d + d * d + d + 1)
     byts = algorithmic_bytes_per_launch(d, k, op.n_cells, op.n_nodes, ncache)
     achieved_tf = flops / (k_ms * 1e-3) / 1e12
+    traffic = TRAFFIC_BYTES_PER_CELL_Q2_3D_FP64 * op.n_cells if (d, k) == (3, 2) else None
     roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_NOMINAL_TFLOPS, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_NOMINAL_TFLOPS, 4), "traffic": traffic,
                 "kernel": f"k_cell_jac<{d},{k},double>", "kernel_ms": round(k_ms, 4),
                 "flops_per_launch": flops, "peak_source": "recipe nominal FP64 1.25 TFLOP/s (probe 1.128)",
                 "hbm": {"achieved_gbs": round(byts / (k_ms * 1e-3) / 1e9, 1),
@@ -287,46 +417,20 @@ def main():
     e2e = {"value": n_dofs * world / (ms_e2e / e2e_steps * 1e-3), "unit": "DoFs/s",
            "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(yh.numel() * 8)}
 
-    # ---- nonlinear step to 1e-8: all-FP64 vs mixed precision (same algorithm:
-    # Newton + FGMRES(20) with an inner Jacobi-GMRES(80) preconditioner whose
-    # operator applies run in FP64 or in FP32).  Initial guess: u^n, p = 0.
+    # ---- nonlinear step to 1e-8: all-FP64 vs mixed precision (same algorithm)
     if not args.no_solve:
-        from paper_2608_27423_b300 import MF_PC_GMRES
-        u0 = np.zeros_like(f["up_star"])
-        u0[:, :d] = f["u_n"]
-        u0[mesh.wall.astype(bool), :d] = 0.0
-        U0 = T(u0)
-        res = {}
-        for name, pcp in (("mixed_fp32_inner", MF_FP32), ("fp64_inner", MF_FP64)):
-            up = U0.clone()
-            o = solver_defaults(theta=prm["theta"], pc=MF_PC_GMRES, pc_precision=pcp, newton_rtol=1e-8,
-                                max_newton=args.max_newton, lin_rtol=1e-2, restart=20, max_lin_iters=60,
-                                inner_iters=80)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st, rep = op.solve_step(up, o)
-            torch.cuda.synchronize()
-            dt_s = time.perf_counter() - t0
-            n_it = rep.newton_iters
-            res[name] = {"status": int(st), "seconds": round(dt_s, 3), "newton_iters": n_it,
-                         "lin_iters": list(rep.lin_iters[:n_it]),
-                         "res_reduction": (rep.res_norm[n_it] / rep.res_norm[0]) if rep.res_norm[0] > 0 else None}
-            print(f"solve {name}: status {st} {dt_s:.2f}s newton {n_it} "
-                  f"res {rep.res_norm[0]:.3e} -> {rep.res_norm[n_it]:.3e}", file=sys.stderr, flush=True)
-            res[name]["solution"] = up
-        a, b = res["fp64_inner"].pop("solution"), res["mixed_fp32_inner"].pop("solution")
-        va, vb = a[:, :d], b[:, :d]
-        pa, pb = a[:, d] - a[:, d].mean(), b[:, d] - b[:, d].mean()
-        res["rel_velocity_diff_mixed_vs_fp64"] = float((va - vb).norm() / va.norm())
-        res["rel_pressure_diff_mixed_vs_fp64_mean_removed"] = float((pa - pb).norm() / pa.norm())
-        extra["solve_to_1e-8"] = res
+        extra["solve_to_1e-8"] = solve_leg(args, op, mesh, prm, f, T)
         op.set_linearization(up_star, prm["theta"])
+
+    if args.batched:
+        extra["batched_12"] = batched_leg(args, T, dev)
 
     line = {"metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: 3D rotor-stator cylinder, {op.n_cells} Q{k} hexes, "
-                                   f"{n_dofs} DoFs, Re=200, BDF2 dt=0.005, theta=0.137, FP64 Jacobian apply",
+            "config": {"workload": f"{args.workload}: {d}D rotor-stator, {op.n_cells} Q{k} cells, "
+                                   f"{n_dofs} DoFs, nu={prm['nu']:.4g}, omega={prm['omega']}, BDF{prm['bdf']} "
+                                   f"dt={prm['dt']}, theta={prm['theta']}, FP64 Jacobian apply",
                        "n_cells": op.n_cells, "n_dofs": n_dofs, "k": k, "d": d,
                        "l2": "inputs larger than L2 (per-point cache ~1.1 GB)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -146,7 +146,7 @@ mf_status mf_diagonal(mf_handle h, void* diag_out, mf_precision prec, void* stre
  *   MF_PC_GMRES      inner_iters steps of Jacobi-preconditioned GMRES (zero initial guess, CGS2)
  *   MF_PC_MG         one V-cycle of the multigrid hierarchy attached with mf_mg_attach (Section 3.4):
  *                    mg_smooth GMRES-Jacobi steps before and after the coarse correction on each
- *                    level, mg_coarse_iters GMRES-Jacobi steps on the coarsest level; always FP32
+ *                    level, mg_coarse_iters GMRES-Jacobi steps on the coarsest level; in pc_precision
  * each applied with pc_precision operator applies (MF_FP32: the FP32 cache). */
 typedef enum { MF_PC_JACOBI = 0, MF_PC_CHEBYSHEV = 1, MF_PC_GMRES = 2, MF_PC_MG = 3 } mf_pc_kind;
 
@@ -166,6 +166,8 @@ typedef struct {
   int    line_search;   /* halve the Newton step up to this many times while ||R|| does not decrease (default 6) */
   int    mg_smooth;     /* MF_PC_MG smoothing steps per level (default 4) */
   int    mg_coarse_iters; /* MF_PC_MG coarsest-level GMRES dimension (default 40) */
+  int    deflate_pressure; /* 1: at each FGMRES restart, minimise the residual along J e_p (the
+                              constant pressure, a near null vector); 0: off (default 0) */
 } mf_solver_opts;
 
 typedef struct {
@@ -216,6 +218,24 @@ mf_status mf_solve_step(mf_handle h, double* up, const mf_solver_opts* so, mf_so
 #define MF_STATIC_WS_DOUBLES (4u << 20)
 mf_status mf_solve_step_static(mf_handle h, double* up, const mf_solver_opts* so, mf_solve_report* rep,
                                void* stream);
+
+/* ---------------------------------------------------------------- batched instances
+ * Several independent operator instances (same d and k; different meshes,
+ * nu, omega, angles) applied in one persistent launch per kernel kind: the
+ * cells (and mortar half-cells) of all instances form one device tile queue
+ * that a grid sized to the GPU drains, so uneven instance sizes balance.
+ * mf_batch_create keeps the handles (caller-owned, at most 64) and allocates
+ * the tile tables; mf_batch_apply_jacobian takes HOST arrays of n device
+ * pointers (xs[i] -> ys[i], each instance's own layout and precision prec) and
+ * is asynchronous on `stream`, except that it waits for the previous call's
+ * table upload to finish before refilling the staging buffer.  Errors:
+ * MF_ERR_ARG (null or aliased pointers, mixed d/k, n out of range),
+ * MF_ERR_STATE (an instance without linearisation). */
+typedef struct mf_batch mf_batch;
+mf_status mf_batch_create(const mf_handle* hs, int n, mf_batch** out);
+mf_status mf_batch_destroy(mf_batch* b);
+mf_status mf_batch_apply_jacobian(mf_batch* b, const void* const* xs, void* const* ys, mf_precision prec,
+                                  void* stream);
 
 /* ---------------------------------------------------------------- multigrid
  * The global-coarsening multigrid of Section 3.4 (geometric and polynomial

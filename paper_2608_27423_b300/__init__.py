@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import MF_FP64, MF_FP32, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
     MfSolverOpts, MfSolveReport
 
-__all__ = ["RotorStatorOperator", "MF_FP64", "MF_FP32", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
+__all__ = ["RotorStatorOperator", "BatchedOperators", "MF_FP64", "MF_FP32", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
            "solver_defaults"]
 
 
@@ -164,3 +164,35 @@ class RotorStatorOperator:
         o = opts if opts is not None else solver_defaults()
         st = self.lib.mf_solve_step(self.h, _ptr(up), C.byref(o), C.byref(rep), _stream(stream))
         return st, rep
+
+
+class BatchedOperators:
+    """Several RotorStatorOperator instances (same d, k) applied in one persistent
+    launch per kernel kind (mf_batch_apply_jacobian)."""
+
+    def __init__(self, ops):
+        lib = _lib.load()
+        self.lib = lib
+        self.ops = list(ops)
+        arr = (C.c_void_p * len(self.ops))(*[o.h.value for o in self.ops])
+        bp = C.c_void_p()
+        _check(lib.mf_batch_create(arr, len(self.ops), C.byref(bp)), None, "mf_batch_create")
+        self.b = bp
+
+    def apply_jacobian(self, xs, ys, prec=MF_FP64, stream=None):
+        n = len(self.ops)
+        xa = (C.c_void_p * n)(*[x.data_ptr() for x in xs])
+        ya = (C.c_void_p * n)(*[y.data_ptr() for y in ys])
+        st = self.lib.mf_batch_apply_jacobian(self.b, xa, ya, int(prec), _stream(stream))
+        _check(st, None, "mf_batch_apply_jacobian")
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.mf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -19,7 +19,8 @@ EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_create", "mf_destroy", "mf
            "mf_set_angle", "mf_node_coords", "mf_dirichlet", "mf_set_history", "mf_set_linearization",
            "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step",
            "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
-           "mf_mg_interpolate", "mf_solve_step_static"]
+           "mf_mg_interpolate", "mf_solve_step_static", "mf_batch_create", "mf_batch_destroy",
+           "mf_batch_apply_jacobian"]
 PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
               "cell_linearization", "dirichlet", "diagonal"]
 
@@ -33,7 +34,8 @@ class MfSolverOpts(C.Structure):
                 ("lin_rtol", C.c_double), ("restart", C.c_int), ("max_lin_iters", C.c_int),
                 ("pc", C.c_int), ("pc_precision", C.c_int), ("cheb_degree", C.c_int),
                 ("cheb_lo", C.c_double), ("theta", C.c_double), ("inner_iters", C.c_int),
-                ("line_search", C.c_int), ("mg_smooth", C.c_int), ("mg_coarse_iters", C.c_int)]
+                ("line_search", C.c_int), ("mg_smooth", C.c_int), ("mg_coarse_iters", C.c_int),
+                ("deflate_pressure", C.c_int)]
 
 
 class MfSolveReport(C.Structure):
@@ -82,6 +84,9 @@ def load():
     lib.mf_solver_defaults.argtypes = [C.POINTER(MfSolverOpts)]
     lib.mf_solver_defaults.restype = None
     lib.mf_solve_step.argtypes = [vp, vp, C.POINTER(MfSolverOpts), C.POINTER(MfSolveReport), vp]
+    lib.mf_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp)]
+    lib.mf_batch_destroy.argtypes = [vp]
+    lib.mf_batch_apply_jacobian.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), i32, vp]
     lib.mf_solve_step_static.argtypes = [vp, vp, C.POINTER(MfSolverOpts), C.POINTER(MfSolveReport), vp]
     lib.mf_mg_attach.argtypes = [vp, vp, vp, vp]
     lib.mf_mg_prolongate.argtypes = [vp, vp, vp, vp]

@@ -92,19 +92,26 @@ template <typename T> __device__ __forceinline__ void atomic_add(T* p, T v) { at
 // dst += J_cell src.  src entries on wall nodes (negative ids in `cells`) are
 // taken as zero for the velocity components.
 template <int D, int K, typename T>
-__global__ void __launch_bounds__(CellCfg<D, K>::THREADS)
-k_cell_jac(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__ cache,
-           const T* __restrict__ src, T* __restrict__ dst, T nu, T a0dt) {
+struct JacSmem {
+  static constexpr int N = K + 1, NQ = ipow(N, D), NS = (D + 1) * D;
+  SmTab<N, T> st;
+  T tile[CellCfg<D, K>::CPB][NS * NQ];
+};
+
+// One block's worth of cells (block index `blk`) of the cell Jacobian.  The
+// tables in sm.st must be loaded and visible to the block.
+template <int D, int K, typename T>
+__device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T>& sm, int64_t blk, const int32_t* __restrict__ cells,
+                                               int64_t nc, const T* __restrict__ cache, const T* __restrict__ src,
+                                               T* __restrict__ dst, T nu, T a0dt) {
   using C = CellCfg<D, K>;
-  constexpr int N = C::N, NQ = C::NQ, NF = D + 1, NS = NF * D;
+  constexpr int N = C::N, NQ = C::NQ, NF = D + 1;
   using CF = Cache<D>;
-  __shared__ SmTab<N, T> st;
-  __shared__ T smem[C::CPB][NS * NQ];
-  load_tab<K, T>(st);
+  SmTab<N, T>& st = sm.st;
   const int cl = threadIdx.x / NQ, t = threadIdx.x % NQ;
-  const int64_t cell = (int64_t)blockIdx.x * C::CPB + cl;
+  const int64_t cell = blk * C::CPB + cl;
   const bool active = cell < nc;
-  T* tile = smem[cl];
+  T* tile = sm.tile[cl];
   int ii[3] = {t % N, (t / N) % N, t / (N * N)};
   const int strd[3] = {1, N, N * N};
 
@@ -279,6 +286,51 @@ k_cell_jac(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__ 
   if (active) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) atomic_add(&dst[(int64_t)node * NF + f], fv[f]);
+  }
+}
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(CellCfg<D, K>::THREADS)
+k_cell_jac(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__ cache,
+           const T* __restrict__ src, T* __restrict__ dst, T nu, T a0dt) {
+  __shared__ JacSmem<D, K, T> sm;
+  load_tab<K, T>(sm.st);
+  cell_jac_block<D, K, T>(sm, blockIdx.x, cells, nc, cache, src, dst, nu, a0dt);
+}
+
+// ---------------------------------------------------------------------------
+// Batched cell Jacobian over several operator instances of the same (D, K):
+// a persistent grid takes tiles (one tile = one block of CPB cells of one
+// instance) from a device counter until all tiles are done; tile -> instance
+// by the prefix table `first_tile` (ninst + 1 entries).  The loop runs a
+// bounded number of times (tiles are finite); it never waits on other blocks.
+template <typename T> struct BatchInst {
+  const int32_t* cells; int64_t nc; const T* cache; const T* src; T* dst; T nu; T a0dt;
+};
+#define MF_BATCH_MAX 64
+template <typename T> struct BatchTable {
+  int ninst;
+  int64_t first_tile[MF_BATCH_MAX + 1];
+  BatchInst<T> inst[MF_BATCH_MAX];
+};
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(CellCfg<D, K>::THREADS)
+k_cell_jac_batched(const BatchTable<T>* __restrict__ tab, unsigned long long* __restrict__ counter) {
+  __shared__ JacSmem<D, K, T> sm;
+  __shared__ long long s_tile;
+  load_tab<K, T>(sm.st);
+  const int64_t total = tab->first_tile[tab->ninst];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= total) break;
+    int i = 0;
+    while (i + 1 < tab->ninst && tab->first_tile[i + 1] <= tile) ++i;
+    const BatchInst<T>& in = tab->inst[i];
+    cell_jac_block<D, K, T>(sm, tile - tab->first_tile[i], in.cells, in.nc, in.cache, in.src, in.dst, in.nu, in.a0dt);
   }
 }
 

@@ -50,6 +50,8 @@ struct Workspace {
   double* c_r = nullptr;
   double* c_d = nullptr;
   double* c_t = nullptr;
+  double* c_v = nullptr;
+  double* c_w = nullptr;
   double* pinned = nullptr;  // host [m+2]
   double* utrial = nullptr;  // [n] Newton line-search trial state
   double* ep = nullptr;      // [n] normalised constant-pressure vector
@@ -272,7 +274,7 @@ extern "C" void mf_mesh_free(mf_mesh* m) { delete m; }
 // ------------------------------------------------------------------ create
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.V, w.Z, w.w, w.r, w.dx, w.hcol, w.part, w.diag64, w.dinv64, w.dinv32, w.f_v, w.f_x, w.f_r,
-                  w.f_d, w.f_t, w.f_w, w.c_x, w.c_r, w.c_d, w.c_t, w.utrial, w.f_Vin, w.c_Vin, w.hin, w.ep, w.jep};
+                  w.f_d, w.f_t, w.f_w, w.c_x, w.c_r, w.c_d, w.c_t, w.c_v, w.c_w, w.utrial, w.f_Vin, w.c_Vin, w.hin, w.ep, w.jep};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (w.pinned) cudaFreeHost(w.pinned);
   if (w.hin_host) cudaFreeHost(w.hin_host);
@@ -514,6 +516,140 @@ extern "C" mf_status mf_profile_read(mf_handle h, mf_profile_t* out) {
 
 #include "mf_solve.inc"
 #include "mf_mg.inc"
+
+// ---------------------------------------------------------------- batched instances
+struct mf_batch {
+  std::vector<mf_ctx*> hs;
+  int d = 0, k = 0;
+  BatchTable<double>* tab64 = nullptr;         // device
+  BatchTable<float>* tab32 = nullptr;
+  MortarBatchTable<double>* mtab64 = nullptr;
+  MortarBatchTable<float>* mtab32 = nullptr;
+  unsigned long long* counters = nullptr;      // device [2]
+  BatchTable<double>* h_tab64 = nullptr;       // pinned host staging
+  BatchTable<float>* h_tab32 = nullptr;
+  MortarBatchTable<double>* h_mtab64 = nullptr;
+  MortarBatchTable<float>* h_mtab32 = nullptr;
+  cudaEvent_t staged = nullptr;                // staging buffers free again
+  int grid_cell = 0, grid_mortar = 0;          // persistent grid sizes
+  std::string err;
+};
+
+template <int D, int K>
+static void batch_grids(mf_batch* b) {
+  int dev = 0, sms = 148, occ_c = 1, occ_m = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, k_cell_jac_batched<D, K, double>, CellCfg<D, K>::THREADS, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_m, k_mortar_batched<D, K, double>, MortarCfg<D, K>::THREADS, 0);
+  b->grid_cell = sms * std::max(occ_c, 1);
+  b->grid_mortar = sms * std::max(occ_m, 1);
+}
+
+extern "C" mf_status mf_batch_create(const mf_handle* hs, int n, mf_batch** out) {
+  if (!hs || !out || n < 1 || n > MF_BATCH_MAX) return MF_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!hs[i] || hs[i]->d != hs[0]->d || hs[i]->k != hs[0]->k) return MF_ERR_ARG;
+  mf_batch* b = new mf_batch();
+  b->hs.assign(hs, hs + n);
+  b->d = hs[0]->d; b->k = hs[0]->k;
+  bool ok = cudaMalloc((void**)&b->tab64, sizeof(BatchTable<double>)) == cudaSuccess &&
+            cudaMalloc((void**)&b->tab32, sizeof(BatchTable<float>)) == cudaSuccess &&
+            cudaMalloc((void**)&b->mtab64, sizeof(MortarBatchTable<double>)) == cudaSuccess &&
+            cudaMalloc((void**)&b->mtab32, sizeof(MortarBatchTable<float>)) == cudaSuccess &&
+            cudaMalloc((void**)&b->counters, 2 * sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMallocHost((void**)&b->h_tab64, sizeof(BatchTable<double>)) == cudaSuccess &&
+            cudaMallocHost((void**)&b->h_tab32, sizeof(BatchTable<float>)) == cudaSuccess &&
+            cudaMallocHost((void**)&b->h_mtab64, sizeof(MortarBatchTable<double>)) == cudaSuccess &&
+            cudaMallocHost((void**)&b->h_mtab32, sizeof(MortarBatchTable<float>)) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    mf_batch_destroy(b);
+    return MF_ERR_OOM;
+  }
+  MF_DISPATCH(b->d, b->k, (batch_grids<D, K>(b)));
+  *out = b;
+  return MF_OK;
+}
+
+extern "C" mf_status mf_batch_destroy(mf_batch* b) {
+  if (!b) return MF_ERR_ARG;
+  void* dp[] = {b->tab64, b->tab32, b->mtab64, b->mtab32, b->counters};
+  for (void* p : dp) if (p) cudaFree(p);
+  void* hp[] = {b->h_tab64, b->h_tab32, b->h_mtab64, b->h_mtab32};
+  for (void* p : hp) if (p) cudaFreeHost(p);
+  if (b->staged) cudaEventDestroy(b->staged);
+  delete b;
+  return MF_OK;
+}
+
+template <typename T>
+static mf_status batch_apply_t(mf_batch* b, const void* const* xs, void* const* ys, cudaStream_t st) {
+  mf_ctx* h = b->hs[0];
+  const bool f64 = std::is_same<T, double>::value;
+  BatchTable<T>* ht = f64 ? (BatchTable<T>*)b->h_tab64 : (BatchTable<T>*)b->h_tab32;
+  BatchTable<T>* dt = f64 ? (BatchTable<T>*)b->tab64 : (BatchTable<T>*)b->tab32;
+  MortarBatchTable<T>* hm = f64 ? (MortarBatchTable<T>*)b->h_mtab64 : (MortarBatchTable<T>*)b->h_mtab32;
+  MortarBatchTable<T>* dm = f64 ? (MortarBatchTable<T>*)b->mtab64 : (MortarBatchTable<T>*)b->mtab32;
+  CK(cudaEventSynchronize(b->staged));    // the previous call's table copies have completed
+  const int n = (int)b->hs.size();
+  int cpb = 1, mpb = 1;
+  switch (b->d * 10 + b->k) {
+#define CASE(D_, K_) case D_ * 10 + K_: cpb = CellCfg<D_, K_>::CPB; mpb = MortarCfg<D_, K_>::MPB; break;
+    CASE(2, 1) CASE(2, 2) CASE(2, 3) CASE(2, 4) CASE(2, 5) CASE(3, 1) CASE(3, 2) CASE(3, 3) CASE(3, 4) CASE(3, 5)
+#undef CASE
+  }
+  ht->ninst = n; hm->ninst = n;
+  ht->first_tile[0] = 0; hm->first_tile[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    mf_ctx* c = b->hs[i];
+    if (!c->have_lin) { b->err = "mf_batch_apply_jacobian: an instance has no linearisation"; return MF_ERR_STATE; }
+    if (!xs[i] || !ys[i] || xs[i] == ys[i]) return MF_ERR_ARG;
+    BatchInst<T>& in = ht->inst[i];
+    in.cells = c->cells; in.nc = c->nc; in.cache = f64 ? (const T*)c->cache64 : (const T*)c->cache32;
+    in.src = (const T*)xs[i]; in.dst = (T*)ys[i]; in.nu = (T)c->nu; in.a0dt = (T)c->a0dt;
+    ht->first_tile[i + 1] = ht->first_tile[i] + (c->nc + cpb - 1) / cpb;
+    MortarArgs<T>& A = hm->inst[i];
+    A.cells = c->cells; A.mc_cell = c->mc_cell; A.mc_tau = c->mc_tau; A.mc_xi = c->mc_xi;
+    A.jinv = f64 ? (const T*)c->mg_jinv64 : (const T*)c->mg_jinv32;
+    A.mc_ang = c->mc_ang; A.mc_w = c->mc_w; A.nm = c->nm; A.src = (const T*)xs[i]; A.dst = (T*)ys[i];
+    A.nu = (T)c->nu; A.dz = c->H / c->n_z; A.zero_wall = 1;
+    hm->first_tile[i + 1] = hm->first_tile[i] + (c->nm + mpb - 1) / mpb;
+    CK(cudaMemsetAsync(ys[i], 0, c->ndof * sizeof(T), st));
+  }
+  CK(cudaMemcpyAsync(dt, ht, sizeof(BatchTable<T>), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dm, hm, sizeof(MortarBatchTable<T>), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(b->staged, st));
+  CK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), st));
+  const int64_t tc = ht->first_tile[n], tm = hm->first_tile[n];
+  switch (b->d * 10 + b->k) {
+#define CASE(D_, K_)                                                                                          \
+  case D_ * 10 + K_:                                                                                          \
+    k_cell_jac_batched<D_, K_, T><<<(unsigned)std::min<int64_t>(tc, b->grid_cell), CellCfg<D_, K_>::THREADS, 0,  \
+                                    st>>>(dt, b->counters);                                                   \
+    k_mortar_batched<D_, K_, T><<<(unsigned)std::min<int64_t>(std::max<int64_t>(tm, 1), b->grid_mortar),        \
+                                  MortarCfg<D_, K_>::THREADS, 0, st>>>(dm, b->counters + 1);                  \
+    break;
+    CASE(2, 1) CASE(2, 2) CASE(2, 3) CASE(2, 4) CASE(2, 5) CASE(3, 1) CASE(3, 2) CASE(3, 3) CASE(3, 4) CASE(3, 5)
+#undef CASE
+  }
+  for (int i = 0; i < n; ++i) {
+    mf_ctx* c = b->hs[i];
+    if (!c->nwall) continue;
+    if (c->d == 2) k_dirichlet_copy<2, T><<<nblk(c->nwall, 256), 256, 0, st>>>(c->wall, c->nwall, (const T*)xs[i], (T*)ys[i]);
+    else k_dirichlet_copy<3, T><<<nblk(c->nwall, 256), 256, 0, st>>>(c->wall, c->nwall, (const T*)xs[i], (T*)ys[i]);
+  }
+  CK(cudaGetLastError());
+  return MF_OK;
+}
+
+extern "C" mf_status mf_batch_apply_jacobian(mf_batch* b, const void* const* xs, void* const* ys, mf_precision prec,
+                                             void* stream) {
+  if (!b || !xs || !ys) return MF_ERR_ARG;
+  mf_status s = prec == MF_FP64 ? batch_apply_t<double>(b, xs, ys, S(stream))
+              : prec == MF_FP32 ? batch_apply_t<float>(b, xs, ys, S(stream)) : MF_ERR_ARG;
+  return s;
+}
 
 // ---------------------------------------------------------------- no-allocation solve
 // Workspace of mf_solve_step_static: a file-scope device array.  In host code

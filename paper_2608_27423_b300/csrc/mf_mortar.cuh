@@ -293,26 +293,34 @@ template <typename T> struct MortarArgs {
   T nu; double dz; int zero_wall;
 };
 
+template <int D, int K, typename T> struct MortarSmem {
+  static constexpr int N = K + 1, NPC = ipow(N, D), NP = ipow(N, D - 1), NF = D + 1,
+                       MPB = MortarCfg<D, K>::MPB;
+  T val[MPB][2][NPC][NF];     // gathered nodal values
+  T fa[MPB][2][NP][NF];       // face-layer values (b1,b2)
+  T fn[MPB][2][NP][NF];       // normal derivative per (b1,b2)
+  T U[MPB][2][NP][NF];        // traces at the points
+  T GU[MPB][2][NP][D][D];     // physical velocity gradients at the points
+  T L1[MPB][2][N][N];         // l_b(xi1 of angular point ia)  [ia][b]
+  T dL1[MPB][2][N][N];
+  T fv[MPB][2][NP][NF];       // value fluxes
+  T Fx[MPB][2][NP][D][D];     // reference gradient fluxes of v
+  T G[MPB][2][NP][NF];        // integrated against face-layer test functions
+  T H[MPB][2][NP][D];         // integrated against normal derivatives
+};
+
+// One block's worth of mortar half-cells (block index `blk`).
 template <int D, int K, typename T, int MODE>
-__global__ void __launch_bounds__(MortarCfg<D, K>::THREADS) k_mortar(MortarArgs<T> A) {
+__device__ __forceinline__ void mortar_block(MortarSmem<D, K, T>& S, int64_t blk, const MortarArgs<T>& A) {
   using C = MortarCfg<D, K>;
-  constexpr int N = C::N, NPC = C::NPC, NP = C::NP, NF = D + 1, MPB = C::MPB;
-  __shared__ T s_val[MPB][2][NPC][NF];     // gathered nodal values
-  __shared__ T s_fa[MPB][2][NP][NF];       // face-layer values (b1,b2)
-  __shared__ T s_fn[MPB][2][NP][NF];       // normal derivative per (b1,b2)
-  __shared__ T s_U[MPB][2][NP][NF];        // traces at the points
-  __shared__ T s_GU[MPB][2][NP][D][D];     // physical velocity gradients at the points
-  __shared__ T s_L1[MPB][2][N][N];         // l_b(xi1 of angular point ia)  [ia][b]
-  __shared__ T s_dL1[MPB][2][N][N];
-  __shared__ T s_fv[MPB][2][NP][NF];       // value fluxes
-  __shared__ T s_Fx[MPB][2][NP][D][D];     // reference gradient fluxes of v
-  __shared__ T s_G[MPB][2][NP][NF];        // integrated against face-layer test functions
-  __shared__ T s_H[MPB][2][NP][D];         // integrated against normal derivatives
+  constexpr int N = C::N, NPC = C::NPC, NP = C::NP, NF = D + 1;
+  auto& s_val = S.val; auto& s_fa = S.fa; auto& s_fn = S.fn; auto& s_U = S.U; auto& s_GU = S.GU;
+  auto& s_L1 = S.L1; auto& s_dL1 = S.dL1; auto& s_fv = S.fv; auto& s_Fx = S.Fx; auto& s_G = S.G; auto& s_H = S.H;
   const MfTab<T>& tb = TabSel<T>::get(K);
   const int lm = threadIdx.x / (2 * NPC);
   const int loc = threadIdx.x % (2 * NPC);
   const int s = loc / NPC, a = loc % NPC;
-  const int64_t mc = (int64_t)blockIdx.x * MPB + lm;
+  const int64_t mc = blk * C::MPB + lm;
   const bool active = mc < A.nm;
   const int fc = (s == 0) ? K : 0;         // index of the face layer along xi_0
   T L0[N], dL0[N];
@@ -519,6 +527,38 @@ __global__ void __launch_bounds__(MortarCfg<D, K>::THREADS) k_mortar(MortarArgs<
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) atomicAdd(&A.dst[(int64_t)node * NF + c], dv);
+  }
+}
+
+template <int D, int K, typename T, int MODE>
+__global__ void __launch_bounds__(MortarCfg<D, K>::THREADS) k_mortar(MortarArgs<T> A) {
+  __shared__ MortarSmem<D, K, T> S;
+  mortar_block<D, K, T, MODE>(S, blockIdx.x, A);
+}
+
+// Batched mortar terms (MODE 0) over several instances: persistent grid,
+// tiles from a device counter, tile -> instance by the prefix table.
+template <typename T> struct MortarBatchTable {
+  int ninst;
+  int64_t first_tile[MF_BATCH_MAX + 1];
+  MortarArgs<T> inst[MF_BATCH_MAX];
+};
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(MortarCfg<D, K>::THREADS)
+k_mortar_batched(const MortarBatchTable<T>* __restrict__ tab, unsigned long long* __restrict__ counter) {
+  __shared__ MortarSmem<D, K, T> S;
+  __shared__ long long s_tile;
+  const int64_t total = tab->first_tile[tab->ninst];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= total) break;
+    int i = 0;
+    while (i + 1 < tab->ninst && tab->first_tile[i + 1] <= tile) ++i;
+    mortar_block<D, K, T, 0>(S, tile - tab->first_tile[i], tab->inst[i]);
   }
 }
 
