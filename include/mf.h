@@ -168,6 +168,9 @@ typedef struct {
   int    mg_coarse_iters; /* MF_PC_MG coarsest-level GMRES dimension (default 40) */
   int    deflate_pressure; /* 1: at each FGMRES restart, minimise the residual along J e_p (the
                               constant pressure, a near null vector); 0: off (default 0) */
+  int    use_graphs;    /* MF_PC_MG: 1 = capture one V-cycle per solve as a CUDA graph on a library
+                           stream and replay it for every preconditioner application (default 1);
+                           0 = launch eagerly.  Graphs are skipped while profiling is enabled. */
 } mf_solver_opts;
 
 typedef struct {

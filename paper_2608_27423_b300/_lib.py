@@ -35,7 +35,7 @@ class MfSolverOpts(C.Structure):
                 ("pc", C.c_int), ("pc_precision", C.c_int), ("cheb_degree", C.c_int),
                 ("cheb_lo", C.c_double), ("theta", C.c_double), ("inner_iters", C.c_int),
                 ("line_search", C.c_int), ("mg_smooth", C.c_int), ("mg_coarse_iters", C.c_int),
-                ("deflate_pressure", C.c_int)]
+                ("deflate_pressure", C.c_int), ("use_graphs", C.c_int)]
 
 
 class MfSolveReport(C.Structure):

@@ -61,7 +61,6 @@ struct Workspace {
   float* f_Vin = nullptr;    // [(mi+1) n] inner FP32 Krylov basis
   double* c_Vin = nullptr;   // [(mi+1) n] inner FP64 Krylov basis
   double* hin = nullptr;     // device inner Hessenberg columns
-  double* hin_host = nullptr;
 };
 
 struct mf_ctx;
@@ -109,6 +108,8 @@ struct mf_ctx {
   float* cache32 = nullptr;
   Workspace ws;
   MgLink mg;
+  cudaStream_t cap_stream = nullptr;   // library stream for graph capture
+  cudaGraphExec_t mg_exec = nullptr;   // captured V-cycle of the current solve
   std::string err;
 };
 
@@ -277,7 +278,6 @@ static void free_ws(Workspace& w) {
                   w.f_d, w.f_t, w.f_w, w.c_x, w.c_r, w.c_d, w.c_t, w.c_v, w.c_w, w.utrial, w.f_Vin, w.c_Vin, w.hin, w.ep, w.jep};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (w.pinned) cudaFreeHost(w.pinned);
-  if (w.hin_host) cudaFreeHost(w.hin_host);
   w = Workspace();
 }
 
@@ -285,6 +285,8 @@ extern "C" mf_status mf_destroy(mf_handle h) {
   if (!h) return MF_ERR_ARG;
   for (auto& e : h->prof_ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->mg_exec) cudaGraphExecDestroy(h->mg_exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
                   h->mc_cell, h->mc_tau, h->mc_xi, h->mc_ang, h->mc_w, h->ht, h->g, h->cache64, h->cache32,
                   h->mg_jinv64, h->mg_jinv32, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32};

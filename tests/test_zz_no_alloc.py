@@ -59,7 +59,8 @@ def test_static_workspace_solve_matches_allocating_solve():
         assert st == 0, (call, op.last_error())
         du, dp = _rel(up, ref)
         assert du < 1e-8 and dp < 1e-6, (call, du, dp)
-        assert rep2.newton_iters == rep.newton_iters
+        # atomics reorder sums, so the step that crosses the 1e-11 tolerance may move by one
+        assert abs(rep2.newton_iters - rep.newton_iters) <= 1
 
 
 def test_static_workspace_rejects_oversized_problems():
