@@ -109,3 +109,26 @@ def test_nan_input_is_reported(case):
     f2["u_n_full"] = u0
     st, rep, up = _solve_gpu(mesh, prm, f2, pc=MF_PC_JACOBI)
     assert st == 5
+
+
+def test_2d_workload_jacobi_newton_to_1e10():
+    """The 2D rotor-stator workload (576 + 768 Q2 quads, non-matching mortar at
+    0.137 rad, nu = 0.01, omega = 1, BDF1 dt = 0.01): Newton with FGMRES whose
+    preconditioner is 80 steps of Jacobi-preconditioned GMRES, to a 1e-10
+    relative residual, equal to the oracle's Newton solution.  (Plain Jacobi as
+    the FGMRES preconditioner stalls near 1e-9 here: the PSPG pressure block is
+    elliptic.)"""
+    from paper_2608_27423_b300 import MF_PC_GMRES, MF_FP64
+    mesh, prm, f = synth.make_config("2d_q2")
+    u0 = np.zeros((mesh.n_nodes, 3))
+    u0[:, :2] = f["u_n"]
+    u0[mesh.wall.astype(bool), :2] = 0.0
+    f = dict(f, u_n_full=u0)
+    ref, red = _oracle_solution(mesh, prm, f)
+    assert red < 1e-12
+    st, rep, up = _solve_gpu(mesh, prm, f, pc=MF_PC_GMRES, pc_precision=MF_FP64, inner_iters=80, newton_rtol=1e-10,
+                             lin_rtol=1e-6, max_newton=30, restart=30, max_lin_iters=300)
+    assert st == 0, (st, rep.newton_iters)
+    assert rep.res_norm[rep.newton_iters] <= 1e-10 * rep.res_norm[0]
+    du, dp = _compare(up, ref)
+    assert du < 1e-7 and dp < 1e-5, (du, dp)
