@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--max-newton", type=int, default=20)
     ap.add_argument("--mg-levels", type=int, default=4)
     ap.add_argument("--batched", action="store_true", help="also time 12 uneven instances, batched vs one by one")
+    ap.add_argument("--transient", type=int, default=0, help="also run this many graph-captured BDF2 time steps")
     return ap.parse_args()
 
 
@@ -191,6 +192,41 @@ def solve_leg(args, op, mesh, prm, f, T):
     if res["mixed_fp32_mg"]["seconds"] > 0:
         res["speedup_mixed_vs_fp64"] = res["fp64_mg"]["seconds"] / res["mixed_fp32_mg"]["seconds"]
     return res
+
+
+# --------------------------------------------------------------------- transient leg
+def transient_leg(args, op, mesh, prm, f, T):
+    """BDF2 time steps with the rotor turning at omega (remap every step), each
+    step 3 Newton iterations x FGMRES(8) preconditioned by the FP32 multigrid
+    V-cycle; the step is captured once as a CUDA graph and replayed.  Reports
+    the time per step (graph vs eager), DoFs/s over the steps, the kinetic
+    energy history and the per-step residual reductions."""
+    import torch
+    from paper_2608_27423_b300 import MF_PC_MG, MF_FP32, solver_defaults
+    from synth.configs import CONFIGS
+    d = mesh.d
+    cfg = CONFIGS[args.workload]
+    if op.__dict__.get("_coarse") is None:
+        build_levels(op, cfg, prm, args.mg_levels - 1)
+    u0 = np.zeros_like(f["up_star"])
+    u0[:, :d] = f["u_n"]
+    u0[mesh.wall.astype(bool), :d] = 0.0
+    o = solver_defaults(pc=MF_PC_MG, pc_precision=MF_FP32, mg_smooth=4, mg_coarse_iters=40)
+    out = {"steps": args.transient, "newton_per_step": 3, "fgmres_per_newton": 8}
+    for label, graph in (("graph", True), ("eager", False)):
+        un, unm1 = T(u0), T(u0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ke, red = op.run_transient(un, unm1, args.transient, prm["theta"], newton_iters=3, krylov_iters=8, opts=o,
+                                   use_graph=graph)
+        torch.cuda.synchronize()
+        dt_s = time.perf_counter() - t0
+        out[label] = {"seconds": round(dt_s, 4), "ms_per_step": 1e3 * dt_s / args.transient,
+                      "dofs_steps_per_s": op.n_dofs * args.transient / dt_s}
+        if graph:
+            out["kinetic_energy"] = [float(x) for x in ke]
+            out["residual_reduction_per_step"] = [float(x) for x in red[1:]]
+    return out
 
 
 # --------------------------------------------------------------------- batched sweep
@@ -424,6 +460,8 @@ def main():
 
     if args.batched:
         extra["batched_12"] = batched_leg(args, T, dev)
+    if args.transient > 0:
+        extra["transient"] = transient_leg(args, op, mesh, prm, f, T)
 
     line = {"metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

@@ -194,6 +194,30 @@ void mf_solver_defaults(mf_solver_opts* o);
 mf_status mf_solve_step(mf_handle h, double* up, const mf_solver_opts* so, mf_solve_report* rep,
                         void* stream);
 
+/* ---------------------------------------------------------------- transient driver
+ * mf_kinetic_energy: ke_dev (device double) = 1/2 int |u|^2 over the mesh at
+ * the current geometry (Gauss rule of the operator); needs the geometry cache
+ * of a previous mf_set_linearization.  Asynchronous.
+ *
+ * mf_run_transient: n_steps BDF steps (the handle's dt and BDF order) starting
+ * at rotor angle theta0, the rotor advancing by omega*dt per step (rotation and
+ * mortar remap every step, Sections 3.1-3.2).  Each step: history term from
+ * (u_n, u_nm1), newton_iters Newton iterations from u_n, each with FGMRES of
+ * fixed dimension krylov_iters (CGS2, device-side least squares) and the
+ * preconditioner of `so` (MF_PC_JACOBI, MF_PC_GMRES or MF_PC_MG with its
+ * precision; Chebyshev is not supported); then u_nm1 <- u_n, u_n <- solution.
+ * No step waits on the host, so with use_graph = 1 one step is captured as a
+ * CUDA graph (on a library stream) and replayed n_steps times on `stream`.
+ * u_n, u_nm1: device [n_nodes][d+1] FP64 (u_nm1 unused for BDF1).  On return
+ * (synchronising) ke_host[0..n_steps] holds the kinetic energy of the initial
+ * state and after each step, red_host[1..n_steps] each step's residual
+ * reduction ||R_end|| / ||R_start|| (either pointer may be NULL).  Errors:
+ * MF_ERR_ARG (dt = 0, counts out of range), MF_ERR_STATE (MG without levels). */
+mf_status mf_kinetic_energy(mf_handle h, const double* up, double* ke_dev, void* stream);
+mf_status mf_run_transient(mf_handle h, double* u_n, double* u_nm1, int n_steps, double theta0, int newton_iters,
+                           int krylov_iters, const mf_solver_opts* so, int use_graph, double* ke_host,
+                           double* red_host, void* stream);
+
 /* ---------------------------------------------------------------- no-allocation solve
  * mf_solve_step_static: the same Newton / FGMRES step as mf_solve_step, for
  * callers that must not allocate device memory during the solve -- e.g. a

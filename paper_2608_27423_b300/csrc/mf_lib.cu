@@ -58,6 +58,11 @@ struct Workspace {
   double* jep = nullptr;     // [n] J e_p
   int mi32 = 0, mi64 = 0;    // inner GMRES dimensions allocated
   int part_cap = 0;          // rows of the partial-sum buffer
+  double* hout = nullptr;    // transient driver: outer Hessenberg columns and scalars (65536 doubles)
+  double* rec_ke = nullptr;  // per-step kinetic energy record
+  double* rec_red = nullptr; // per-step residual reduction record
+  int* rec_count = nullptr;
+  int rec_cap = 0;
   float* f_Vin = nullptr;    // [(mi+1) n] inner FP32 Krylov basis
   double* c_Vin = nullptr;   // [(mi+1) n] inner FP64 Krylov basis
   double* hin = nullptr;     // device inner Hessenberg columns
@@ -109,6 +114,9 @@ struct mf_ctx {
   Workspace ws;
   MgLink mg;
   cudaStream_t cap_stream = nullptr;   // library stream for graph capture
+  double* d_theta = nullptr;           // device copy of the rotor angle (transient driver)
+  bool own_theta = false;              // d_theta allocated by this handle
+  bool theta_on_dev = false;           // kernels read the angle from d_theta
   cudaGraphExec_t mg_exec = nullptr;   // captured V-cycle of the current solve
   std::string err;
 };
@@ -229,7 +237,7 @@ static void launch_map(mf_ctx* h, cudaStream_t st) {
   MortarMap A;
   A.mc_cell = h->mc_cell; A.mc_tau = h->mc_tau; A.mc_xi = h->mc_xi; A.mc_ang = h->mc_ang; A.mc_w = h->mc_w;
   A.ifr = h->ifr; A.ifs = h->ifs; A.tau_r = h->tau_r; A.tau_s = h->tau_s; A.n_R = h->n_R; A.n_z = h->n_z;
-  A.R = h->R; A.phi0 = h->phi0; A.theta = h->theta;
+  A.R = h->R; A.phi0 = h->phi0; A.theta = h->theta; A.theta_dev = h->theta_on_dev ? h->d_theta : nullptr;
   k_mortar_map<K><<<nblk(h->nm, 128), 128, 0, st>>>(A);
 }
 
@@ -275,7 +283,8 @@ extern "C" void mf_mesh_free(mf_mesh* m) { delete m; }
 // ------------------------------------------------------------------ create
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.V, w.Z, w.w, w.r, w.dx, w.hcol, w.part, w.diag64, w.dinv64, w.dinv32, w.f_v, w.f_x, w.f_r,
-                  w.f_d, w.f_t, w.f_w, w.c_x, w.c_r, w.c_d, w.c_t, w.c_v, w.c_w, w.utrial, w.f_Vin, w.c_Vin, w.hin, w.ep, w.jep};
+                  w.f_d, w.f_t, w.f_w, w.c_x, w.c_r, w.c_d, w.c_t, w.c_v, w.c_w, w.utrial, w.f_Vin, w.c_Vin, w.hin, w.ep, w.jep,
+                  w.hout, w.rec_ke, w.rec_red, w.rec_count};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (w.pinned) cudaFreeHost(w.pinned);
   w = Workspace();
@@ -286,6 +295,7 @@ extern "C" mf_status mf_destroy(mf_handle h) {
   for (auto& e : h->prof_ev) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
   for (auto e : h->ev_pool) cudaEventDestroy(e);
   if (h->mg_exec) cudaGraphExecDestroy(h->mg_exec);
+  if (h->d_theta && h->own_theta) cudaFree(h->d_theta);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
                   h->mc_cell, h->mc_tau, h->mc_xi, h->mc_ang, h->mc_w, h->ht, h->g, h->cache64, h->cache32,
@@ -301,8 +311,9 @@ extern "C" const char* mf_last_error(mf_handle h) { return h ? h->err.c_str() : 
 static mf_status apply_angle(mf_ctx* h, double theta, cudaStream_t st) {
   h->theta = theta;
   const double ct = cos(theta), sn = sin(theta);
-  if (h->d == 2) k_rotate<2><<<nblk(h->nn, 256), 256, 0, st>>>(h->x0, h->node_side, h->x, h->nn, ct, sn);
-  else k_rotate<3><<<nblk(h->nn, 256), 256, 0, st>>>(h->x0, h->node_side, h->x, h->nn, ct, sn);
+  const double* td = h->theta_on_dev ? h->d_theta : nullptr;
+  if (h->d == 2) k_rotate<2><<<nblk(h->nn, 256), 256, 0, st>>>(h->x0, h->node_side, h->x, h->nn, ct, sn, td);
+  else k_rotate<3><<<nblk(h->nn, 256), 256, 0, st>>>(h->x0, h->node_side, h->x, h->nn, ct, sn, td);
   switch (h->k) {
     case 1: launch_map<1>(h, st); break;
     case 2: launch_map<2>(h, st); break;
@@ -368,8 +379,8 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
       cudaMemset(h->ht, 0, nn * d * 8) != cudaSuccess)
     return fail(MF_ERR_CUDA);
   // geometry at theta = 0, penalties (rotation-invariant), mortar cells
-  if (h->d == 2) k_rotate<2><<<nblk(h->nn, 256), 256>>>(h->x0, h->node_side, h->x, h->nn, 1.0, 0.0);
-  else k_rotate<3><<<nblk(h->nn, 256), 256>>>(h->x0, h->node_side, h->x, h->nn, 1.0, 0.0);
+  if (h->d == 2) k_rotate<2><<<nblk(h->nn, 256), 256>>>(h->x0, h->node_side, h->x, h->nn, 1.0, 0.0, nullptr);
+  else k_rotate<3><<<nblk(h->nn, 256), 256>>>(h->x0, h->node_side, h->x, h->nn, 1.0, 0.0, nullptr);
   MF_DISPATCH(h->d, h->k, (launch_penalty<D, K>(h, 0)));
   if (apply_angle(h, 0.0, 0) != MF_OK) return fail(MF_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) { h->err = cudaGetErrorString(cudaGetLastError()); return fail(MF_ERR_CUDA); }
@@ -518,6 +529,7 @@ extern "C" mf_status mf_profile_read(mf_handle h, mf_profile_t* out) {
 
 #include "mf_solve.inc"
 #include "mf_mg.inc"
+#include "mf_transient.inc"
 
 // ---------------------------------------------------------------- batched instances
 struct mf_batch {

@@ -29,9 +29,10 @@ __device__ __forceinline__ void lagrange_at(const MfTab<T>& tb, T t, T* L, T* dL
 // R = cos I + sin W + (1 - cos) r (x) r with axis r = e_z), x = x0 otherwise.
 template <int D>
 __global__ void k_rotate(const double* __restrict__ x0, const uint8_t* __restrict__ side, double* __restrict__ x,
-                         int64_t nn, double ct, double st) {
+                         int64_t nn, double ct, double st, const double* __restrict__ theta_dev) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nn) return;
+  if (theta_dev) { ct = cos(*theta_dev); st = sin(*theta_dev); }   // angle kept on the device (graph replays)
   double p[3] = {x0[i * D], x0[i * D + 1], D == 3 ? x0[i * D + 2] : 0.0};
   if (side[i] == 0) {
     const double r[3] = {0.0, 0.0, 1.0};
@@ -70,6 +71,7 @@ struct MortarMap {
   const double* tau_s;
   int n_R, n_z;
   double R, phi0, theta;
+  const double* theta_dev;   // if set, the angle is read from device memory
 };
 
 template <int K>
@@ -82,8 +84,9 @@ __global__ void k_mortar_map(MortarMap A) {
   const int js = (int)((m >> 1) % A.n_R);
   const int lz = (int)((m >> 1) / A.n_R);
   const double Dl = 2.0 * M_PI / A.n_R;
-  const double sf = floor(A.theta / Dl);
-  double th = A.theta - sf * Dl;
+  const double theta = A.theta_dev ? *A.theta_dev : A.theta;
+  const double sf = floor(theta / Dl);
+  double th = theta - sf * Dl;
   if (th < 0.0) th = 0.0;
   if (th > Dl) th = Dl;
   long long si = (long long)sf % A.n_R;

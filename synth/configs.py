@@ -11,6 +11,8 @@
   (6.69M DoFs); Re = 200.
 * ``3d_q2_mid``: the 3d_q2 physics on m=16, n_r=4, n_s=8, n_z=16 (16,384 hexes,
   0.56M DoFs; per-point cache 124 MB) for profiling and solver checks.
+* ``3d_q3_1m``: large cylinder, m=48, n_r=16, n_s=32, n_z=88 -> 1,013,760 Q3 hexes
+  (110.8M DoFs), Re = 2000, BDF2 dt = 0.002 (apply throughput at scale).
 * small variants for tests.
 """
 import numpy as np
@@ -27,6 +29,8 @@ CONFIGS = {
                       dt=0.005, bdf=2, theta=0.137, state="smooth"),
     "3d_q3": dict(d=3, k=3, m=24, n_r=8, n_s=12, n_z=24, nu=1.0 / (400.0 * np.pi), omega=1.0,
                   dt=0.005, bdf=2, theta=0.137, state="smooth"),
+    "3d_q3_1m": dict(d=3, k=3, m=48, n_r=16, n_s=32, n_z=88, nu=1.0 / (4000.0 * np.pi), omega=1.0,
+                     dt=0.002, bdf=2, theta=0.137, state="smooth"),
 }
 
 
