@@ -123,6 +123,21 @@ def build_inputs(workload):
     return mesh, prm, f
 
 
+# --------------------------------------------------------------------- ranks
+def aggregate_ranks(ms_local, dofs_local, dist=None, device=None):
+    """Whole-job timing over replica ranks: the slowest rank's time and the DoFs
+    all ranks processed per step (each rank runs its own instance; no data-path
+    collective, only this reduction of two scalars)."""
+    if dist is None:
+        return float(ms_local), float(dofs_local)
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(dofs_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 # --------------------------------------------------------------------- solve leg
 def build_levels(op, cfg, prm, n_h):
     """Multigrid levels below `op`: one polynomial level (k -> k-1) when k >= 3,
@@ -167,11 +182,13 @@ def solve_leg(args, op, mesh, prm, f, T):
     U0 = T(u0)
     res = {"levels": [f"Q{lv.k}:{lv.n_cells}" for lv in levels]}
     sols = {}
-    for name, pcp in (("mixed_fp32_mg", MF_FP32), ("fp64_mg", MF_FP64)):
+    from paper_2608_27423_b300 import MF_DF64
+    for name, pcp, outer in (("mixed_fp32_mg", MF_FP32, MF_FP64), ("fp64_mg", MF_FP64, MF_FP64),
+                             ("mixed_fp32_mg_df64_outer", MF_FP32, MF_DF64)):
         up = U0.clone()
         o = solver_defaults(theta=prm["theta"], pc=MF_PC_MG, pc_precision=pcp, newton_rtol=1e-8,
                             max_newton=args.max_newton, lin_rtol=1e-2, restart=30, max_lin_iters=150,
-                            mg_smooth=4, mg_coarse_iters=40)
+                            mg_smooth=4, mg_coarse_iters=40, outer_precision=outer)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, rep = op.solve_step(up, o)
@@ -396,13 +413,9 @@ def main():
     prof = op.profile_read()
     op.profile(False)
     clocks = sampler.stop(local)
-    t_max = ms
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max, dofs_all = aggregate_ranks(ms, n_dofs, dist, dev)
     ms_step = t_max / args.steps
-    value = n_dofs * world / (ms_step * 1e-3)
+    value = dofs_all / (ms_step * 1e-3)
 
     # dominant kernel roofline (FP64 cell Jacobian, bound by the FP64 pipe)
     nl, kms = prof["cell_jac_fp64"]
@@ -431,6 +444,12 @@ def main():
     y32 = torch.empty_like(x32)
     ms32 = timed(lambda: op.apply_jacobian(x32, y32, prec=MF_FP32), args.steps, 3)
     extra["fp32_apply_dofs_per_s"] = n_dofs / (ms32 / args.steps * 1e-3)
+    # ---- FP64-accurate apply in double-float arithmetic on the FP32 pipes
+    from paper_2608_27423_b300 import MF_DF64
+    ydf = torch.empty_like(x)
+    msdf = timed(lambda: op.apply_jacobian(x, ydf, prec=MF_DF64), args.steps, 3)
+    extra["df64_apply_dofs_per_s"] = n_dofs / (msdf / args.steps * 1e-3)
+    extra["df64_vs_fp64_rel_diff"] = float((ydf - y).norm() / y.norm())
     # ---- residual and linearisation set-up
     r = torch.empty_like(x)
     msr = timed(lambda: op.residual(up_star, r), max(10, args.steps // 10), 2)

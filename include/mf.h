@@ -53,7 +53,11 @@ typedef enum {
   MF_ERR_ITER_LIMIT = 8    /* reserved: device-side loop hit its hard cap */
 } mf_status;
 
-typedef enum { MF_FP64 = 0, MF_FP32 = 1 } mf_precision;
+/* MF_FP64: native FP64 arithmetic.  MF_FP32: FP32 arithmetic on an FP32 copy of
+ * the cache (vectors are float).  MF_DF64: FP64-accurate applies computed in
+ * double-float arithmetic (pairs of floats, ~48-bit significand) on the FP32
+ * pipes, FP64 vectors in memory; only mf_apply_jacobian accepts it. */
+typedef enum { MF_FP64 = 0, MF_FP32 = 1, MF_DF64 = 2 } mf_precision;
 
 /* ---------------------------------------------------------------- mesh
  * mf_mesh_from_arrays: copy a merged rotor-stator mesh from HOST arrays.
@@ -131,7 +135,8 @@ mf_status mf_set_linearization(mf_handle h, const double* up_star, double theta,
 mf_status mf_residual(mf_handle h, const double* up, double* r, void* stream);
 
 /* y = J x at the current linearisation.  prec MF_FP64: x, y double; MF_FP32:
- * x, y float (FP32 cache).  x entries on wall velocity DoFs are ignored as
+ * x, y float (FP32 cache); MF_DF64: x, y double, double-float arithmetic (its
+ * cache copy is built on the first such call after each linearisation).  x entries on wall velocity DoFs are ignored as
  * inputs and copied to y (identity rows/columns).  x and y must not alias. */
 mf_status mf_apply_jacobian(mf_handle h, const void* x, void* y, mf_precision prec, void* stream);
 
@@ -171,6 +176,8 @@ typedef struct {
   int    use_graphs;    /* MF_PC_MG: 1 = capture one V-cycle per solve as a CUDA graph on a library
                            stream and replay it for every preconditioner application (default 1);
                            0 = launch eagerly.  Graphs are skipped while profiling is enabled. */
+  int    outer_precision; /* Jacobian applies of the outer FGMRES: MF_FP64 (default) or MF_DF64
+                             (FP64-accurate double-float on the FP32 pipes) */
 } mf_solver_opts;
 
 typedef struct {
@@ -231,7 +238,7 @@ mf_status mf_run_transient(mf_handle h, double* u_n, double* u_nm1, int n_steps,
  * MF_STATIC_WS_DOUBLES doubles (32 MiB) that every GPU which loads libmf.so
  * holds until the process exits.  The call allocates no device or pinned host
  * memory: no cudaMalloc, cudaFree, cudaMallocHost or event creation.  Limits:
- *   - pc must be MF_PC_JACOBI with pc_precision MF_FP64;
+ *   - pc must be MF_PC_JACOBI with pc_precision MF_FP64 and outer_precision MF_FP64;
  *   - (2*restart + 10) * n_dofs + 3*(restart + 2) + (restart + 2) * 592 doubles
  *     must fit in the array, otherwise MF_ERR_ARG with a message (e.g. 2D
  *     workloads of ~16k DoFs with restart <= 100);

@@ -9,10 +9,10 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import MF_FP64, MF_FP32, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
+from ._lib import MF_FP64, MF_FP32, MF_DF64, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
     MfSolverOpts, MfSolveReport
 
-__all__ = ["RotorStatorOperator", "BatchedOperators", "MF_FP64", "MF_FP32", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
+__all__ = ["RotorStatorOperator", "BatchedOperators", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
            "solver_defaults"]
 
 

@@ -11,7 +11,7 @@ MF_OK, MF_ERR_ARG, MF_ERR_CUDA, MF_ERR_OOM, MF_ERR_STATE, MF_ERR_NAN, MF_ERR_NOT
     MF_ERR_BREAKDOWN, MF_ERR_ITER_LIMIT = range(9)
 STATUS_NAMES = ["MF_OK", "MF_ERR_ARG", "MF_ERR_CUDA", "MF_ERR_OOM", "MF_ERR_STATE", "MF_ERR_NAN",
                 "MF_ERR_NOT_CONVERGED", "MF_ERR_BREAKDOWN", "MF_ERR_ITER_LIMIT"]
-MF_FP64, MF_FP32 = 0, 1
+MF_FP64, MF_FP32, MF_DF64 = 0, 1, 2
 MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG = 0, 1, 2, 3
 
 # every symbol include/mf.h declares
@@ -35,7 +35,7 @@ class MfSolverOpts(C.Structure):
                 ("pc", C.c_int), ("pc_precision", C.c_int), ("cheb_degree", C.c_int),
                 ("cheb_lo", C.c_double), ("theta", C.c_double), ("inner_iters", C.c_int),
                 ("line_search", C.c_int), ("mg_smooth", C.c_int), ("mg_coarse_iters", C.c_int),
-                ("deflate_pressure", C.c_int), ("use_graphs", C.c_int)]
+                ("deflate_pressure", C.c_int), ("use_graphs", C.c_int), ("outer_precision", C.c_int)]
 
 
 class MfSolveReport(C.Structure):

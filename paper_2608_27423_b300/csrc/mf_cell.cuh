@@ -11,6 +11,11 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "mf_tables.h"
+#include "mf_df64.cuh"
+
+#ifndef MF_DF_MINB
+#define MF_DF_MINB 2
+#endif
 
 namespace mf {
 
@@ -50,8 +55,10 @@ template <typename T> struct TabSel;
 // Defined once: the library is a single translation unit.
 __constant__ MfTab<double> c_tab64[MF_KMAX + 1];
 __constant__ MfTab<float> c_tab32[MF_KMAX + 1];
+__constant__ MfTab<df> c_tabdf[MF_KMAX + 1];
 template <> struct TabSel<double> { __device__ static const MfTab<double>& get(int k) { return c_tab64[k]; } };
 template <> struct TabSel<float> { __device__ static const MfTab<float>& get(int k) { return c_tab32[k]; } };
+template <> struct TabSel<df> { __device__ static const MfTab<df>& get(int k) { return c_tabdf[k]; } };
 
 // Shared copies of the 1D matrices for degree K.
 template <int N, typename T> struct SmTab {
@@ -85,7 +92,7 @@ __device__ __forceinline__ void line(const T* __restrict__ tile, int NQ, int t, 
   }
 }
 
-template <typename T> __device__ __forceinline__ void atomic_add(T* p, T v) { atomicAdd(p, v); }
+template <typename T> __device__ __forceinline__ void atomic_add(typename IO<T>::type* p, T v) { atomicAdd(p, to_io<T>(v)); }
 
 // ---------------------------------------------------------------------------
 // Jacobian apply, volume part (blocks A-hat .. D-hat of Section 2.3, tau frozen).
@@ -102,8 +109,9 @@ struct JacSmem {
 // tables in sm.st must be loaded and visible to the block.
 template <int D, int K, typename T>
 __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T>& sm, int64_t blk, const int32_t* __restrict__ cells,
-                                               int64_t nc, const T* __restrict__ cache, const T* __restrict__ src,
-                                               T* __restrict__ dst, T nu, T a0dt) {
+                                               int64_t nc, const T* __restrict__ cache,
+                                               const typename IO<T>::type* __restrict__ src,
+                                               typename IO<T>::type* __restrict__ dst, T nu, T a0dt) {
   using C = CellCfg<D, K>;
   constexpr int N = C::N, NQ = C::NQ, NF = D + 1;
   using CF = Cache<D>;
@@ -122,7 +130,7 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T>& sm, int64_t blk
     const bool wall = id < 0;
     node = wall ? ~id : id;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) v[f] = src[(int64_t)node * NF + f];
+    for (int f = 0; f < NF; ++f) v[f] = from_io<T>(src[(int64_t)node * NF + f]);
     if (wall) {
 #pragma unroll
       for (int c = 0; c < D; ++c) v[c] = T(0);
@@ -289,10 +297,15 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T>& sm, int64_t blk
   }
 }
 
+// Minimum resident blocks requested from the register allocator: the
+// double-float variant is latency-bound at one block per SM otherwise.
+template <typename T> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<df> { static constexpr int value = MF_DF_MINB; };
+
 template <int D, int K, typename T>
-__global__ void __launch_bounds__(CellCfg<D, K>::THREADS)
+__global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MinBlocks<T>::value)
 k_cell_jac(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__ cache,
-           const T* __restrict__ src, T* __restrict__ dst, T nu, T a0dt) {
+           const typename IO<T>::type* __restrict__ src, typename IO<T>::type* __restrict__ dst, T nu, T a0dt) {
   __shared__ JacSmem<D, K, T> sm;
   load_tab<K, T>(sm.st);
   cell_jac_block<D, K, T>(sm, blockIdx.x, cells, nc, cache, src, dst, nu, a0dt);
@@ -305,7 +318,8 @@ k_cell_jac(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__ 
 // by the prefix table `first_tile` (ninst + 1 entries).  The loop runs a
 // bounded number of times (tiles are finite); it never waits on other blocks.
 template <typename T> struct BatchInst {
-  const int32_t* cells; int64_t nc; const T* cache; const T* src; T* dst; T nu; T a0dt;
+  const int32_t* cells; int64_t nc; const T* cache; const typename IO<T>::type* src; typename IO<T>::type* dst;
+  T nu; T a0dt;
 };
 #define MF_BATCH_MAX 64
 template <typename T> struct BatchTable {

@@ -108,6 +108,9 @@ struct mf_ctx {
   double *mc_tau = nullptr, *mc_xi = nullptr, *mc_ang = nullptr, *mc_w = nullptr;
   double* mg_jinv64 = nullptr;   // face geometry J^-1 at the mortar points [M][2][NP][d][d]
   float* mg_jinv32 = nullptr;
+  df* mg_jinvdf = nullptr;       // double-float copies for MF_DF64 (built on demand)
+  df* cachedf = nullptr;
+  bool df_valid = false;
   double *ht = nullptr, *g = nullptr;
   double* cache64 = nullptr;
   float* cache32 = nullptr;
@@ -156,14 +159,18 @@ static mf_status upload_tables(mf_ctx* h) {
   if (dev < 64 && g_tabs_ready[dev]) return MF_OK;
   MfTab<double> t64[MF_KMAX + 1];
   MfTab<float> t32[MF_KMAX + 1];
+  MfTab<df> tdf[MF_KMAX + 1];
   std::memset(t64, 0, sizeof(t64));
   std::memset(t32, 0, sizeof(t32));
+  std::memset(tdf, 0, sizeof(tdf));
   for (int k = 1; k <= MF_KMAX; ++k) {
     mfhost::build_tab(k, t64[k]);
     mfhost::cast_tab(t64[k], t32[k]);
+    mfhost::cast_tab(t64[k], tdf[k]);
   }
   CK(cudaMemcpyToSymbol(c_tab64, t64, sizeof(t64)));
   CK(cudaMemcpyToSymbol(c_tab32, t32, sizeof(t32)));
+  CK(cudaMemcpyToSymbol(c_tabdf, tdf, sizeof(tdf)));
   if (dev < 64) g_tabs_ready[dev] = true;
   return MF_OK;
 }
@@ -197,7 +204,8 @@ static void launch_state(mf_ctx* h, int mode, const double* up, double* dst, cud
 }
 
 template <int D, int K, typename T>
-static void launch_jac(mf_ctx* h, const T* cache, const T* x, T* y, cudaStream_t st) {
+static void launch_jac(mf_ctx* h, const T* cache, const typename IO<T>::type* x, typename IO<T>::type* y,
+                       cudaStream_t st) {
   using C = CellCfg<D, K>;
   const unsigned g = nblk(h->nc, C::CPB);
   ProfScope ps(h, std::is_same<T, double>::value ? 0 : 1, st);
@@ -205,10 +213,12 @@ static void launch_jac(mf_ctx* h, const T* cache, const T* x, T* y, cudaStream_t
 }
 
 template <int D, int K, typename T>
-static void launch_mortar(mf_ctx* h, int mode, const T* src, T* dst, int zero_wall, cudaStream_t st) {
+static void launch_mortar(mf_ctx* h, int mode, const typename IO<T>::type* src, typename IO<T>::type* dst,
+                          int zero_wall, cudaStream_t st) {
   MortarArgs<T> A;
   A.cells = h->cells; A.mc_cell = h->mc_cell; A.mc_tau = h->mc_tau; A.mc_xi = h->mc_xi;
-  A.jinv = std::is_same<T, double>::value ? (const T*)h->mg_jinv64 : (const T*)h->mg_jinv32;
+  A.jinv = std::is_same<T, double>::value ? (const T*)h->mg_jinv64
+         : std::is_same<T, float>::value ? (const T*)h->mg_jinv32 : (const T*)h->mg_jinvdf;
   A.mc_ang = h->mc_ang; A.mc_w = h->mc_w; A.nm = h->nm; A.src = src; A.dst = dst; A.nu = (T)h->nu;
   A.dz = h->H / h->n_z; A.zero_wall = zero_wall;
   using C = MortarCfg<D, K>;
@@ -299,7 +309,7 @@ extern "C" mf_status mf_destroy(mf_handle h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
                   h->mc_cell, h->mc_tau, h->mc_xi, h->mc_ang, h->mc_w, h->ht, h->g, h->cache64, h->cache32,
-                  h->mg_jinv64, h->mg_jinv32, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32};
+                  h->mg_jinv64, h->mg_jinv32, h->mg_jinvdf, h->cachedf, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32};
   for (void* p : ptrs) if (p) cudaFree(p);
   free_ws(h->ws);
   delete h;
@@ -310,6 +320,7 @@ extern "C" const char* mf_last_error(mf_handle h) { return h ? h->err.c_str() : 
 
 static mf_status apply_angle(mf_ctx* h, double theta, cudaStream_t st) {
   h->theta = theta;
+  h->df_valid = false;
   const double ct = cos(theta), sn = sin(theta);
   const double* td = h->theta_on_dev ? h->d_theta : nullptr;
   if (h->d == 2) k_rotate<2><<<nblk(h->nn, 256), 256, 0, st>>>(h->x0, h->node_side, h->x, h->nn, ct, sn, td);
@@ -440,6 +451,7 @@ extern "C" mf_status mf_set_linearization(mf_handle h, const double* up_star, do
   k_cast<double, float><<<nblk(ncv, 256), 256, 0, st>>>(h->cache64, h->cache32, ncv);
   CK(cudaGetLastError());
   h->have_lin = true;
+  h->df_valid = false;
   return MF_OK;
 }
 
@@ -458,17 +470,33 @@ extern "C" mf_status mf_residual(mf_handle h, const double* up, double* r, void*
 }
 
 template <typename T>
-static mf_status apply_t(mf_ctx* h, const T* x, T* y, cudaStream_t st) {
-  const T* cache = std::is_same<T, double>::value ? (const T*)h->cache64 : (const T*)h->cache32;
-  CK(cudaMemsetAsync(y, 0, h->ndof * sizeof(T), st));
+static mf_status apply_t(mf_ctx* h, const typename IO<T>::type* x, typename IO<T>::type* y, cudaStream_t st) {
+  using TI = typename IO<T>::type;
+  const T* cache = std::is_same<T, double>::value ? (const T*)h->cache64
+                 : std::is_same<T, float>::value ? (const T*)h->cache32 : (const T*)h->cachedf;
+  CK(cudaMemsetAsync(y, 0, h->ndof * sizeof(TI), st));
   MF_DISPATCH(h->d, h->k, (launch_jac<D, K, T>(h, cache, x, y, st)));
   MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 0, x, y, 1, st)));
   if (h->nwall) {
     ProfScope ps(h, 6, st);
-    if (h->d == 2) k_dirichlet_copy<2, T><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, x, y);
-    else k_dirichlet_copy<3, T><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, x, y);
+    if (h->d == 2) k_dirichlet_copy<2, TI><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, x, y);
+    else k_dirichlet_copy<3, TI><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, x, y);
   }
   CK(cudaGetLastError());
+  return MF_OK;
+}
+
+// double-float copies of the linearisation cache and the face geometry
+static mf_status ensure_df(mf_ctx* h, cudaStream_t st) {
+  const int64_t ncv = (int64_t)h->ncache * h->nc * ipow(h->k + 1, h->d);
+  const int64_t njv = h->nm * 2 * ipow(h->k + 1, h->d - 1) * h->d * h->d;
+  if (!h->cachedf) CK(cudaMalloc((void**)&h->cachedf, sizeof(df) * ncv));
+  if (!h->mg_jinvdf) CK(cudaMalloc((void**)&h->mg_jinvdf, sizeof(df) * njv));
+  if (h->df_valid) return MF_OK;
+  k_split_df<<<nblk(ncv, 256), 256, 0, st>>>(h->cache64, h->cachedf, ncv);
+  k_split_df<<<nblk(njv, 256), 256, 0, st>>>(h->mg_jinv64, h->mg_jinvdf, njv);
+  CK(cudaGetLastError());
+  h->df_valid = true;
   return MF_OK;
 }
 
@@ -477,6 +505,11 @@ extern "C" mf_status mf_apply_jacobian(mf_handle h, const void* x, void* y, mf_p
   if (!h->have_lin) { h->err = "mf_apply_jacobian before mf_set_linearization"; return MF_ERR_STATE; }
   if (prec == MF_FP64) return apply_t<double>(h, (const double*)x, (double*)y, S(stream));
   if (prec == MF_FP32) return apply_t<float>(h, (const float*)x, (float*)y, S(stream));
+  if (prec == MF_DF64) {
+    mf_status e = ensure_df(h, S(stream));
+    if (e != MF_OK) return e;
+    return apply_t<df>(h, (const double*)x, (double*)y, S(stream));
+  }
   return MF_ERR_ARG;
 }
 
@@ -678,8 +711,8 @@ extern "C" mf_status mf_solve_step_static(mf_handle h, double* up, const mf_solv
   if (!h || !up) return MF_ERR_ARG;
   mf_solver_opts so;
   if (so_in) so = *so_in; else mf_solver_defaults(&so);
-  if (so.pc != MF_PC_JACOBI || so.pc_precision != MF_FP64) {
-    h->err = "mf_solve_step_static: only pc = MF_PC_JACOBI with pc_precision = MF_FP64";
+  if (so.pc != MF_PC_JACOBI || so.pc_precision != MF_FP64 || so.outer_precision != MF_FP64) {
+    h->err = "mf_solve_step_static: only pc = MF_PC_JACOBI with pc_precision = MF_FP64 (FP64 outer applies)";
     return MF_ERR_ARG;
   }
   if (h->prof) { h->err = "mf_solve_step_static: disable profiling (it creates events)"; return MF_ERR_STATE; }

@@ -292,7 +292,7 @@ template <typename T> struct MortarArgs {
   const int32_t* mc_cell; const double* mc_tau; const double* mc_xi; const double* mc_ang; const double* mc_w;
   const T* jinv;      // [M][2][NP][D][D]
   int64_t nm;
-  const T* src; T* dst;
+  const typename IO<T>::type* src; typename IO<T>::type* dst;
   T nu; double dz; int zero_wall;
 };
 
@@ -337,7 +337,7 @@ __device__ __forceinline__ void mortar_block(MortarSmem<D, K, T>& S, int64_t blk
     node = wall ? ~id : id;
     if (MODE == 0) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) s_val[lm][s][a][f] = A.src[(int64_t)node * NF + f];
+      for (int f = 0; f < NF; ++f) s_val[lm][s][a][f] = from_io<T>(A.src[(int64_t)node * NF + f]);
       if (wall && A.zero_wall) {
 #pragma unroll
         for (int c = 0; c < D; ++c) s_val[lm][s][a][c] = T(0);
@@ -497,7 +497,7 @@ __device__ __forceinline__ void mortar_block(MortarSmem<D, K, T>& S, int64_t blk
     for (int c = 0; c < D; ++c) out[c] = fma(L0[a0], s_G[lm][s][q][c], dL0[a0] * s_H[lm][s][q][c]);
     out[D] = L0[a0] * s_G[lm][s][q][D];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) atomicAdd(&A.dst[(int64_t)node * NF + f], out[f]);
+    for (int f = 0; f < NF; ++f) atomic_add(&A.dst[(int64_t)node * NF + f], out[f]);
   } else {
     // ---- diagonal: w nu [tau phi^2 - phi (grad phi . n_s)] on face nodes, per velocity component
     if (!active) return;
@@ -529,7 +529,7 @@ __device__ __forceinline__ void mortar_block(MortarSmem<D, K, T>& S, int64_t blk
       dv += w * A.nu * (tau_f * phi * phi - phi * gn);
     }
 #pragma unroll
-    for (int c = 0; c < D; ++c) atomicAdd(&A.dst[(int64_t)node * NF + c], dv);
+    for (int c = 0; c < D; ++c) atomic_add(&A.dst[(int64_t)node * NF + c], dv);
   }
 }
 

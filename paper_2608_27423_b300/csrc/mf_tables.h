@@ -113,12 +113,14 @@ inline void build_tab(int k, MfTab<double>& T) {
     }
 }
 
+template <typename T> inline T cast_to(double x) { return (T)x; }
+
 template <typename T>
 inline void cast_tab(const MfTab<double>& A, MfTab<T>& B) {
   for (int i = 0; i < MF_NMAX; ++i) {
-    B.s[i] = (T)A.s[i]; B.w[i] = (T)A.w[i]; B.gll[i] = (T)A.gll[i]; B.bw[i] = (T)A.bw[i];
+    B.s[i] = T(A.s[i]); B.w[i] = T(A.w[i]); B.gll[i] = T(A.gll[i]); B.bw[i] = T(A.bw[i]);
     for (int j = 0; j < MF_NMAX; ++j) {
-      B.B[i][j] = (T)A.B[i][j]; B.Dn[i][j] = (T)A.Dn[i][j]; B.Hn[i][j] = (T)A.Hn[i][j]; B.Dg[i][j] = (T)A.Dg[i][j];
+      B.B[i][j] = T(A.B[i][j]); B.Dn[i][j] = T(A.Dn[i][j]); B.Hn[i][j] = T(A.Hn[i][j]); B.Dg[i][j] = T(A.Dg[i][j]);
     }
   }
 }

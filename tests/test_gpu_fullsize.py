@@ -64,6 +64,9 @@ def test_fullsize_sampled_rows(name):
     g.apply_jacobian(x, y)
     y32 = torch.empty_like(x, dtype=torch.float32)
     g.apply_jacobian(x.float(), y32, prec=MF_FP32)
+    from paper_2608_27423_b300 import MF_DF64
+    ydf = torch.empty_like(x)
+    g.apply_jacobian(x, ydf, prec=MF_DF64)
     r = torch.empty_like(x)
     g.residual(T(f["up_star"]), r)
     rng = np.random.default_rng(7)
@@ -71,6 +74,8 @@ def test_fullsize_sampled_rows(name):
     yj = _rows_oracle(mesh, prm, f, nodes, f["x"], "jac")
     yr = _rows_oracle(mesh, prm, f, nodes, f["up_star"], "res")
     y = y.cpu().numpy()[nodes]
+    ydf = ydf.cpu().numpy()[nodes]
+    assert np.linalg.norm(ydf - yj) <= 1e-12 * np.linalg.norm(yj)
     y32 = y32.double().cpu().numpy()[nodes]
     r = r.cpu().numpy()[nodes]
     assert np.linalg.norm(y - yj) <= 1e-12 * np.linalg.norm(yj)

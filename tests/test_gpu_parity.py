@@ -74,6 +74,17 @@ def test_jacobian_fp32_matches_oracle(c):
     assert rel(y.double().cpu().numpy(), y_ref) <= TOL32
 
 
+@pytest.mark.parametrize("c", CASES, ids=lambda c: f"d{c['d']}k{c['k']}")
+def test_jacobian_df64_matches_oracle_at_fp64_bar(c):
+    """Double-float applies (FP32 pipes) meet the FP64 bar."""
+    mesh, prm, f, op, g, T = setup(**c)
+    y_ref = op.apply(f["x"])
+    y = torch.empty_like(T(f["x"]))
+    from paper_2608_27423_b300 import MF_DF64
+    g.apply_jacobian(T(f["x"]), y, prec=MF_DF64)
+    assert rel(y.cpu().numpy(), y_ref) <= TOL64
+
+
 @pytest.mark.parametrize("c", CASES[:5], ids=lambda c: f"d{c['d']}k{c['k']}")
 def test_diagonal_matches_assembled(c):
     mesh, prm, f, op, g, T = setup(**c)
