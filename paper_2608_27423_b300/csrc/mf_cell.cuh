@@ -16,6 +16,9 @@
 #ifndef MF_DF_MINB
 #define MF_DF_MINB 2
 #endif
+#ifndef MF_F32_MINB
+#define MF_F32_MINB 5
+#endif
 
 namespace mf {
 
@@ -301,6 +304,7 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T>& sm, int64_t blk
 // double-float variant is latency-bound at one block per SM otherwise.
 template <typename T> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<df> { static constexpr int value = MF_DF_MINB; };
+template <> struct MinBlocks<float> { static constexpr int value = MF_F32_MINB; };
 
 template <int D, int K, typename T>
 __global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MinBlocks<T>::value)
