@@ -66,7 +66,9 @@ typedef enum { MF_FP64 = 0, MF_FP32 = 1, MF_DF64 = 2 } mf_precision;
  *   n_nodes, x0  [n_nodes][d] node coordinates in the reference (theta = 0)
  *                configuration
  *   node_side    [n_nodes] 0 = rotor node (rotates), 1 = stator node
- *   wall         [n_nodes] 1 = velocity Dirichlet node
+ *   wall         [n_nodes] 0 = free, 1 = stationary velocity Dirichlet node,
+ *                2 = wall moving with the rotor (e.g. a blade; a rotor node):
+ *                Dirichlet velocity omega e_z x x at the node's current position
  *   n_cells, cells [n_cells][(k+1)^d] int32 node ids, tensor order with xi_0
  *                fastest; every cell map must have positive Jacobian
  *   cell_side    [n_cells] 0 = rotor cell (mesh velocity omega e_z x x), 1 = stator
@@ -80,7 +82,8 @@ typedef enum { MF_FP64 = 0, MF_FP32 = 1, MF_DF64 = 2 } mf_precision;
  *                xi_0 radial outward, xi_1 counter-clockwise angle, xi_2 = z;
  *                the interface face is xi_0 = 1 (rotor) / xi_0 = 0 (stator).
  * The library copies everything; the caller may free its arrays on return.
- * Errors: MF_ERR_ARG for null pointers, d/k out of range, ids out of range.
+ * Errors: MF_ERR_ARG for null pointers, d/k out of range, ids out of range,
+ * wall values above 2.
  */
 mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const double* x0,
                               const uint8_t* node_side, const uint8_t* wall,
@@ -117,7 +120,9 @@ mf_status mf_set_angle(mf_handle h, double theta, void* stream);
 /* Current node coordinates, device out [n_nodes][d]. */
 mf_status mf_node_coords(mf_handle h, double* xyz_out, void* stream);
 
-/* Dirichlet values g (device [n_nodes][d], read at wall nodes), NULL = zero. */
+/* Dirichlet values g (device [n_nodes][d], read at stationary wall nodes,
+ * wall = 1), NULL = zero.  Walls moving with the rotor (wall = 2) always take
+ * the rigid rotation omega e_z x x of the current angle instead. */
 mf_status mf_dirichlet(mf_handle h, const double* g, void* stream);
 
 /* BDF history (device [n_nodes][d] each; u_nm1 ignored/NULL for BDF1):
@@ -206,6 +211,12 @@ mf_status mf_solve_step(mf_handle h, double* up, const mf_solver_opts* so, mf_so
  * the current geometry (Gauss rule of the operator); needs the geometry cache
  * of a previous mf_set_linearization.  Asynchronous.
  *
+ * mf_energy: the energy budget terms of up at the current geometry, out_dev
+ * (device double[2]): out_dev[0] = 1/2 int |u|^2, out_dev[1] = nu int
+ * grad u : grad u (the viscous dissipation of the Laplacian form of the
+ * viscous term, Eq. 1), Gauss rule of the operator, wall values included.
+ * Needs the geometry cache (mf_set_linearization).  Asynchronous.
+ *
  * mf_run_transient: n_steps BDF steps (the handle's dt and BDF order) starting
  * at rotor angle theta0, the rotor advancing by omega*dt per step (rotation and
  * mortar remap every step, Sections 3.1-3.2).  Each step: history term from
@@ -216,14 +227,16 @@ mf_status mf_solve_step(mf_handle h, double* up, const mf_solver_opts* so, mf_so
  * No step waits on the host, so with use_graph = 1 one step is captured as a
  * CUDA graph (on a library stream) and replayed n_steps times on `stream`.
  * u_n, u_nm1: device [n_nodes][d+1] FP64 (u_nm1 unused for BDF1).  On return
- * (synchronising) ke_host[0..n_steps] holds the kinetic energy of the initial
+ * (synchronising) ke_host[0..n_steps] and diss_host[0..n_steps] hold the
+ * kinetic energy and the viscous dissipation (as mf_energy) of the initial
  * state and after each step, red_host[1..n_steps] each step's residual
- * reduction ||R_end|| / ||R_start|| (either pointer may be NULL).  Errors:
+ * reduction ||R_end|| / ||R_start|| (any of the three may be NULL).  Errors:
  * MF_ERR_ARG (dt = 0, counts out of range), MF_ERR_STATE (MG without levels). */
 mf_status mf_kinetic_energy(mf_handle h, const double* up, double* ke_dev, void* stream);
+mf_status mf_energy(mf_handle h, const double* up, double* out_dev, void* stream);
 mf_status mf_run_transient(mf_handle h, double* u_n, double* u_nm1, int n_steps, double theta0, int newton_iters,
                            int krylov_iters, const mf_solver_opts* so, int use_graph, double* ke_host,
-                           double* red_host, void* stream);
+                           double* diss_host, double* red_host, void* stream);
 
 /* ---------------------------------------------------------------- no-allocation solve
  * mf_solve_step_static: the same Newton / FGMRES step as mf_solve_step, for

@@ -104,6 +104,25 @@ class Problem:
         xq = np.einsum("Kam,qa->Kqm", X, self.phi)
         return dict(J=J, detJ=detJ, Jinv=Jinv, W=W, grad=grad, lap=lap, xq=xq)
 
+    def energy(self, up):
+        """Energy budget terms of the discrete velocity u_h at the current
+        geometry, by the operator's Gauss rule: kinetic energy 1/2 int |u_h|^2
+        and viscous dissipation nu int grad u_h : grad u_h (the dissipation of
+        the Laplacian form of the viscous term in Eq. 1).  Wall values count."""
+        up = np.asarray(up, dtype=np.float64).reshape(self.nn, -1)
+        d = self.d
+        ke = diss = 0.0
+        nc = self.cells.shape[0]
+        for s0 in range(0, nc, 512):
+            cl = np.arange(s0, min(nc, s0 + 512))
+            g = self.geometry(cl)
+            U = up[self.cells[cl]][..., :d]                              # [C,N,d]
+            uq = np.einsum("qa,Kai->Kqi", self.phi, U)
+            gu = np.einsum("Kqam,Kai->Kqim", g["grad"], U)
+            ke += 0.5 * float((g["W"] * (uq ** 2).sum(-1)).sum())
+            diss += self.nu * float((g["W"] * (gu ** 2).sum((-1, -2))).sum())
+        return ke, diss
+
     def cell_size(self, cl):
         """h = diameter of the area- (2D) / volume- (3D) equivalent circle/sphere
         (Eq. Eq-stab-param; 3D reading S9)."""

@@ -34,8 +34,14 @@ class Operator:
         cm = np.zeros((self.nn, self.d + 1), dtype=bool)
         cm[self.wall, :self.d] = True
         self.cmask = cm
-        # Dirichlet values g [N_n, d] on wall nodes (zero unless given)
-        self.g = np.zeros((self.nn, self.d)) if g is None else np.asarray(g, dtype=np.float64)
+        # Dirichlet values g [N_n, d] on wall nodes (zero unless given); walls moving with the
+        # rotor (wall = 2) take the rigid-rotation velocity omega e_z x x at the current angle
+        self.g = np.zeros((self.nn, self.d)) if g is None else np.array(g, dtype=np.float64)
+        mv = np.asarray(mesh.wall) == 2
+        if mv.any():
+            x = self.prob.x
+            self.g[mv, 0] = -self.prob.omega * x[mv, 1]
+            self.g[mv, 1] = self.prob.omega * x[mv, 0]
 
     def set_linearization(self, up_star):
         self.up_star = np.asarray(up_star, dtype=np.float64)

@@ -160,18 +160,24 @@ class RotorStatorOperator:
         """out (1-element device FP64 tensor) = 1/2 int |u|^2."""
         self._chk(self.lib.mf_kinetic_energy(self.h, _ptr(up), _ptr(out), _stream(stream)), "mf_kinetic_energy")
 
+    def energy(self, up, out, stream=None):
+        """out (2-element device FP64 tensor) = (1/2 int |u|^2, nu int grad u : grad u)."""
+        self._chk(self.lib.mf_energy(self.h, _ptr(up), _ptr(out), _stream(stream)), "mf_energy")
+
     def run_transient(self, u_n, u_nm1, n_steps, theta0, newton_iters=3, krylov_iters=6, opts=None,
                       use_graph=True, stream=None):
         """n_steps BDF steps with the rotor turning (see mf_run_transient); returns
-        (kinetic energies [n_steps+1], residual reductions [n_steps+1])."""
+        (kinetic energies, viscous dissipations, residual reductions), each [n_steps+1]."""
         ke = np.zeros(n_steps + 1)
+        diss = np.zeros(n_steps + 1)
         red = np.zeros(n_steps + 1)
         o = opts if opts is not None else solver_defaults()
         st = self.lib.mf_run_transient(self.h, _ptr(u_n), _ptr(u_nm1) if u_nm1 is not None else None, int(n_steps),
                                        float(theta0), int(newton_iters), int(krylov_iters), C.byref(o),
-                                       int(bool(use_graph)), _np_ptr(ke), _np_ptr(red), _stream(stream))
+                                       int(bool(use_graph)), _np_ptr(ke), _np_ptr(diss), _np_ptr(red),
+                                       _stream(stream))
         self._chk(st, "mf_run_transient")
-        return ke, red
+        return ke, diss, red
 
     def last_error(self):
         return self.lib.mf_last_error(self.h).decode()

@@ -60,6 +60,7 @@ struct Workspace {
   int part_cap = 0;          // rows of the partial-sum buffer
   double* hout = nullptr;    // transient driver: outer Hessenberg columns and scalars (65536 doubles)
   double* rec_ke = nullptr;  // per-step kinetic energy record
+  double* rec_diss = nullptr;  // per-step viscous dissipation record
   double* rec_red = nullptr; // per-step residual reduction record
   int* rec_count = nullptr;
   int rec_cap = 0;
@@ -96,6 +97,7 @@ struct mf_ctx {
   double R = 0, H = 1, phi0 = 0, theta = 0;
   int n_R = 0, n_z = 1;
   int64_t nm = 0, nwall = 0, nif = 0;
+  int64_t nmwall = 0;  // the last nmwall entries of `wall` move with the rotor (blade walls)
   bool have_lin = false;
   int ncache = 0;
   int nb = 0;  // blocks for reductions
@@ -276,6 +278,8 @@ extern "C" mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const do
   m->x0.assign(x0, x0 + n_nodes * d);
   m->node_side.assign(node_side, node_side + n_nodes);
   m->wall.assign(wall, wall + n_nodes);
+  for (uint8_t w : m->wall)
+    if (w > 2) { delete m; return MF_ERR_ARG; }
   m->cells.assign(cells, cells + n_cells * npc);
   m->cell_side.assign(cell_side, cell_side + n_cells);
   m->ifr.assign(iface_rotor, iface_rotor + (int64_t)n_z * n_R);
@@ -294,7 +298,7 @@ extern "C" void mf_mesh_free(mf_mesh* m) { delete m; }
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.V, w.Z, w.w, w.r, w.dx, w.hcol, w.part, w.diag64, w.dinv64, w.dinv32, w.f_v, w.f_x, w.f_r,
                   w.f_d, w.f_t, w.f_w, w.c_x, w.c_r, w.c_d, w.c_t, w.c_v, w.c_w, w.utrial, w.f_Vin, w.c_Vin, w.hin, w.ep, w.jep,
-                  w.hout, w.rec_ke, w.rec_red, w.rec_count};
+                  w.hout, w.rec_ke, w.rec_diss, w.rec_red, w.rec_count};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (w.pinned) cudaFreeHost(w.pinned);
   w = Workspace();
@@ -360,9 +364,12 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
   // cell table with wall nodes encoded as ~id
   std::vector<int32_t> cells(m->cells);
   for (auto& c : cells) if (m->wall[c]) c = ~c;
+  // wall list: stationary walls first, then the walls moving with the rotor
   std::vector<int32_t> wl;
-  for (int64_t i = 0; i < m->nn; ++i) if (m->wall[i]) wl.push_back((int32_t)i);
+  for (int64_t i = 0; i < m->nn; ++i) if (m->wall[i] == 1) wl.push_back((int32_t)i);
+  for (int64_t i = 0; i < m->nn; ++i) if (m->wall[i] == 2) wl.push_back((int32_t)i);
   h->nwall = (int64_t)wl.size();
+  h->nmwall = h->nwall - (int64_t)std::count(m->wall.begin(), m->wall.end(), (uint8_t)1);
   const size_t nn = m->nn, nc = m->nc, d = m->d;
 #define ALLOC(p, cnt) CK(cudaMalloc((void**)&(p), sizeof(*(p)) * std::max<size_t>(1, (size_t)(cnt))))
   auto fail = [&](mf_status st) { std::string e = h->err; mf_destroy(h); (void)e; return st; };
@@ -462,8 +469,9 @@ extern "C" mf_status mf_residual(mf_handle h, const double* up, double* r, void*
   MF_DISPATCH(h->d, h->k, (launch_state<D, K>(h, 1, up, r, st)));
   MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, double>(h, 0, up, r, 0, st)));
   if (h->nwall) {
-    if (h->d == 2) k_dirichlet_res<2><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, up, h->g, r);
-    else k_dirichlet_res<3><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, up, h->g, r);
+    const int64_t m0 = h->nwall - h->nmwall;
+    if (h->d == 2) k_dirichlet_res<2><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, m0, up, h->g, h->x, h->omega, r);
+    else k_dirichlet_res<3><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, m0, up, h->g, h->x, h->omega, r);
   }
   CK(cudaGetLastError());
   return MF_OK;

@@ -23,15 +23,27 @@ __global__ void k_dirichlet_copy(const int32_t* __restrict__ wall, int64_t nw, c
 #pragma unroll
   for (int c = 0; c < D; ++c) y[n * (D + 1) + c] = x[n * (D + 1) + c];
 }
-// Residual: r = u - g on wall velocity DoFs.
+// Residual: r = u - g on wall velocity DoFs.  Entries i >= m0 of the wall
+// list move with the rotor: there g is the rigid rotation omega e_z x x at
+// the current node position x (the mesh velocity of Section 3.1).
 template <int D>
-__global__ void k_dirichlet_res(const int32_t* __restrict__ wall, int64_t nw, const double* __restrict__ up,
-                                const double* __restrict__ g, double* __restrict__ r) {
+__global__ void k_dirichlet_res(const int32_t* __restrict__ wall, int64_t nw, int64_t m0, const double* __restrict__ up,
+                                const double* __restrict__ g, const double* __restrict__ x, double omega,
+                                double* __restrict__ r) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nw) return;
   const int64_t n = wall[i];
+  double gv[D];
+  if (i >= m0) {
+    gv[0] = -omega * x[n * D + 1];
+    gv[1] = omega * x[n * D + 0];
+    if (D == 3) gv[D - 1] = 0.0;
+  } else {
 #pragma unroll
-  for (int c = 0; c < D; ++c) r[n * (D + 1) + c] = up[n * (D + 1) + c] - (g ? g[n * D + c] : 0.0);
+    for (int c = 0; c < D; ++c) gv[c] = g ? g[n * D + c] : 0.0;
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) r[n * (D + 1) + c] = up[n * (D + 1) + c] - gv[c];
 }
 // diag = 1 on wall velocity DoFs.
 template <int D, typename T>

@@ -12,7 +12,8 @@
 * ``3d_q2_mid``: the 3d_q2 physics on m=16, n_r=4, n_s=8, n_z=16 (16,384 hexes,
   0.56M DoFs; per-point cache 124 MB) for profiling and solver checks.
 * ``3d_q3_1m``: large cylinder, m=48, n_r=16, n_s=32, n_z=88 -> 1,013,760 Q3 hexes
-  (110.8M DoFs), Re = 2000, BDF2 dt = 0.002 (apply throughput at scale).
+  (110.8M DoFs), Re = 2000, BDF2 dt = 0.002, four radial blades inside the
+  rotor (walls moving with it); apply throughput at scale and transient steps.
 * small variants for tests.
 """
 import numpy as np
@@ -30,7 +31,7 @@ CONFIGS = {
     "3d_q3": dict(d=3, k=3, m=24, n_r=8, n_s=12, n_z=24, nu=1.0 / (400.0 * np.pi), omega=1.0,
                   dt=0.005, bdf=2, theta=0.137, state="smooth"),
     "3d_q3_1m": dict(d=3, k=3, m=48, n_r=16, n_s=32, n_z=88, nu=1.0 / (4000.0 * np.pi), omega=1.0,
-                     dt=0.002, bdf=2, theta=0.137, state="smooth"),
+                     dt=0.002, bdf=2, theta=0.137, state="smooth", blades=4),
 }
 
 
@@ -43,7 +44,7 @@ def make_config(name=None, seed=SEED, **over):
     cfg = dict(CONFIGS[name]) if name else {}
     cfg.update(over)
     d, k = cfg["d"], cfg["k"]
-    mesh = rotor_stator_mesh(d, k, cfg["m"], cfg["n_r"], cfg["n_s"], cfg.get("n_z", 1))
+    mesh = rotor_stator_mesh(d, k, cfg["m"], cfg["n_r"], cfg["n_s"], cfg.get("n_z", 1), blades=cfg.get("blades", 0))
     N = mesh.n_nodes
     if cfg.get("state", "iid") == "iid":
         up = __import__("synth.fields", fromlist=["x"]).random_nodal_field(N, d + 1, seed)

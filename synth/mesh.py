@@ -59,7 +59,7 @@ class RotorStatorMesh:
     cells: np.ndarray         # [N_c, (k+1)^d] int32, tensor order, xi_0 fastest
     cell_side: np.ndarray     # [N_c] uint8, 0 rotor, 1 stator
     node_side: np.ndarray     # [N_n] uint8, 0 rotor, 1 stator
-    wall: np.ndarray          # [N_n] uint8, 1 = homogeneous Dirichlet velocity
+    wall: np.ndarray          # [N_n] uint8, 1 = stationary wall, 2 = wall moving with the rotor (blade)
     iface_rotor: np.ndarray   # [n_z, n_R] int32
     iface_stator: np.ndarray  # [n_z, n_R] int32
     R: float
@@ -83,8 +83,13 @@ class RotorStatorMesh:
 
 
 def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55,
-                      phi0=-0.25 * np.pi):
-    """Generate the merged rotor/stator mesh (see module docstring)."""
+                      phi0=-0.25 * np.pi, blades=0):
+    """Generate the merged rotor/stator mesh (see module docstring).
+
+    blades > 0 (3D): that many radial blades inside the rotor, each the ring
+    cells of one angular index (equally spaced), the inner three quarters of
+    the rings and the middle half of the height; their nodes are walls moving
+    with the rotor (wall = 2, velocity omega e_z x x)."""
     if d not in (2, 3):
         raise ValueError("d must be 2 or 3")
     g = _gll01(k)
@@ -178,7 +183,7 @@ def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55
     ifr2 = ring_cell_index[:, n_r - 1]
     ifs2 = st_cell_index[:, 0]
 
-    params = dict(d=d, k=k, m=m, n_r=n_r, n_s=n_s, n_z=n_z, R=R, R_out=R_out, H=H, sq=sq, phi0=phi0)
+    params = dict(d=d, k=k, m=m, n_r=n_r, n_s=n_s, n_z=n_z, R=R, R_out=R_out, H=H, sq=sq, phi0=phi0, blades=blades)
     if d == 2:
         return RotorStatorMesh(d=2, k=k, x0=xy.copy(), cells=cells2.astype(np.int32),
                                cell_side=cell_side2, node_side=node_side2, wall=wall2,
@@ -187,6 +192,12 @@ def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55
                                R=R, n_R=n_R, n_z=1, H=1.0, phi0=phi0, params=params)
 
     # ---- 3D extrusion: node id = iz * n2 + id2, cell id = lz * n_c2 + c2
+    blade_cells2 = []
+    if blades > 0:
+        for b in range(blades):
+            j = (b * n_R) // blades
+            for jr in range(0, max(1, (3 * n_r) // 4)):
+                blade_cells2.append(ring_cell_index[j, jr])
     zs = H * _param(n_z, k, g)
     nz_nodes = n_z * k + 1
     x3 = np.empty((nz_nodes, n2, 3))
@@ -194,6 +205,10 @@ def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55
     x3[:, :, 2] = zs[:, None]
     x3 = x3.reshape(-1, 3)
     wall3 = np.tile(wall2, nz_nodes)
+    if blade_cells2:
+        bnodes2 = np.unique(cells2[blade_cells2].ravel())
+        for iz in range((n_z // 4) * k, (3 * n_z // 4) * k + 1):
+            wall3[iz * n2 + bnodes2] = 2
     wall3[:n2] = 1
     wall3[(nz_nodes - 1) * n2:] = 1
     node_side3 = np.tile(node_side2, nz_nodes)

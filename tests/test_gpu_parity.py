@@ -20,10 +20,10 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def setup(d, k, m, n_r, n_s, n_z=1, bdf=2, theta=0.137, nu=0.05, omega=1.0, dt=0.01, state="iid", seed=11):
+def setup(d, k, m, n_r, n_s, n_z=1, bdf=2, theta=0.137, nu=0.05, omega=1.0, dt=0.01, state="iid", seed=11, blades=0):
     from paper_2608_27423_b300 import RotorStatorOperator
     mesh, prm, f = synth.make_config(d=d, k=k, m=m, n_r=n_r, n_s=n_s, n_z=n_z, nu=nu, omega=omega, dt=dt, bdf=bdf,
-                                     theta=theta, state=state, seed=seed)
+                                     theta=theta, state=state, seed=seed, blades=blades)
     op = make_op(mesh, prm, f)
     g = RotorStatorOperator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
     dev = torch.device("cuda")
@@ -41,10 +41,15 @@ CASES = [
     dict(d=3, k=2, m=2, n_r=1, n_s=2, n_z=3),
     dict(d=3, k=3, m=1, n_r=1, n_s=2, n_z=2, theta=0.9),
     dict(d=3, k=1, m=2, n_r=2, n_s=2, n_z=3),
+    dict(d=3, k=2, m=2, n_r=4, n_s=2, n_z=4, theta=0.7, omega=1.3, blades=4),    # blades: walls moving with the rotor
 ]
 
 
-@pytest.mark.parametrize("c", CASES, ids=lambda c: f"d{c['d']}k{c['k']}")
+def cid(c):
+    return f"d{c['d']}k{c['k']}" + ("blades" if c.get("blades") else "")
+
+
+@pytest.mark.parametrize("c", CASES, ids=cid)
 def test_jacobian_fp64_matches_oracle(c):
     mesh, prm, f, op, g, T = setup(**c)
     y_ref = op.apply(f["x"])
@@ -53,7 +58,7 @@ def test_jacobian_fp64_matches_oracle(c):
     assert rel(y.cpu().numpy(), y_ref) <= TOL64
 
 
-@pytest.mark.parametrize("c", CASES, ids=lambda c: f"d{c['d']}k{c['k']}")
+@pytest.mark.parametrize("c", CASES, ids=cid)
 def test_residual_matches_oracle(c):
     mesh, prm, f, op, g, T = setup(**c)
     up = f["up_star"] * 0.7 + 0.1
@@ -63,7 +68,7 @@ def test_residual_matches_oracle(c):
     assert rel(r.cpu().numpy(), r_ref) <= TOL64
 
 
-@pytest.mark.parametrize("c", CASES[:5], ids=lambda c: f"d{c['d']}k{c['k']}")
+@pytest.mark.parametrize("c", CASES[:5], ids=cid)
 def test_jacobian_fp32_matches_oracle(c):
     mesh, prm, f, op, g, T = setup(**c)
     y_ref = op.apply(f["x"])
@@ -74,7 +79,7 @@ def test_jacobian_fp32_matches_oracle(c):
     assert rel(y.double().cpu().numpy(), y_ref) <= TOL32
 
 
-@pytest.mark.parametrize("c", CASES, ids=lambda c: f"d{c['d']}k{c['k']}")
+@pytest.mark.parametrize("c", CASES, ids=cid)
 def test_jacobian_df64_matches_oracle_at_fp64_bar(c):
     """Double-float applies (FP32 pipes) meet the FP64 bar."""
     mesh, prm, f, op, g, T = setup(**c)
@@ -85,13 +90,27 @@ def test_jacobian_df64_matches_oracle_at_fp64_bar(c):
     assert rel(y.cpu().numpy(), y_ref) <= TOL64
 
 
-@pytest.mark.parametrize("c", CASES[:5], ids=lambda c: f"d{c['d']}k{c['k']}")
+@pytest.mark.parametrize("c", CASES[:5], ids=cid)
 def test_diagonal_matches_assembled(c):
     mesh, prm, f, op, g, T = setup(**c)
     dref = op.diagonal()
     dg = torch.empty_like(T(f["x"]))
     g.diagonal(dg)
     assert rel(dg.cpu().numpy(), dref) <= TOL64
+
+
+@pytest.mark.parametrize("c", CASES, ids=cid)
+def test_energy_matches_oracle(c):
+    """mf_energy (kinetic energy, viscous dissipation) and mf_kinetic_energy."""
+    mesh, prm, f, op, g, T = setup(**c)
+    up = f["up_star"] * 0.7 + 0.1
+    ke_ref, di_ref = op.prob.energy(up)
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    g.energy(T(up), out)
+    ke, di = out.cpu().numpy()
+    assert abs(ke / ke_ref - 1) <= TOL64 and abs(di / di_ref - 1) <= TOL64, (ke, ke_ref, di, di_ref)
+    g.kinetic_energy(T(up), out[:1])
+    assert abs(float(out[0]) / ke_ref - 1) <= TOL64
 
 
 def test_node_coordinates_follow_rotation():

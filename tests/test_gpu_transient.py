@@ -103,10 +103,10 @@ def test_transient_driver_graph_replay_equals_eager(pc):
         un, unm1 = T(u0), T(um1)
         o = solver_defaults(pc=MF_PC_MG if pc == "mg" else MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=30,
                             mg_smooth=4, mg_coarse_iters=40)
-        ke, red = ops[0].run_transient(un, unm1, 6, 0.137, newton_iters=4, krylov_iters=15, opts=o,
-                                       use_graph=use_graph)
-        res[use_graph] = (un.cpu().numpy(), ke, red)
-    (a, ke_a, red_a), (b, ke_b, red_b) = res[False], res[True]
+        ke, diss, red = ops[0].run_transient(un, unm1, 6, 0.137, newton_iters=4, krylov_iters=15, opts=o,
+                                             use_graph=use_graph)
+        res[use_graph] = (un.cpu().numpy(), ke, red, diss)
+    (a, ke_a, red_a, diss_a), (b, ke_b, red_b, diss_b) = res[False], res[True]
     # both runs solve every step to the fixed iteration budget; atomics reorder sums and the FP32
     # inner solves pass those roundoff differences on at the level of the step tolerance.  The
     # pressure level is fixed only weakly (the constant pressure is a near null vector), so
@@ -116,5 +116,35 @@ def test_transient_driver_graph_replay_equals_eager(pc):
     dp = np.linalg.norm(pa - pb) / np.linalg.norm(pa)
     assert dv < 1e-6 and dp < 1e-5, (dv, dp, red_a, red_b)
     assert np.allclose(ke_a, ke_b, rtol=1e-7)
+    assert np.allclose(diss_a, diss_b, rtol=1e-5) and np.all(diss_b > 0.0)
     assert np.all(red_b[1:] < 1e-6), red_b
     assert np.all(np.diff(ke_b[1:]) < 0.0), ke_b
+
+
+def test_transient_blades_move_with_the_rotor():
+    """Blades (walls moving with the rotor, wall = 2) hold the rigid velocity
+    omega e_z x x of the angle each graph-replayed step reaches; the fluid they
+    stir from rest gains kinetic energy and dissipates it."""
+    from paper_2608_27423_b300 import RotorStatorOperator, solver_defaults, MF_PC_GMRES, MF_FP32
+    mesh = synth.rotor_stator_mesh(3, 2, 4, 2, 2, 4, blades=4)
+    omega, theta0, dt, steps = 1.0, 0.2, 0.01, 4
+    op = RotorStatorOperator(mesh, 0.01, omega, dt, 2)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    u0 = np.zeros((mesh.n_nodes, 4))
+    un, unm1 = T(u0), T(u0)
+    o = solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=30)
+    ke, diss, red = op.run_transient(un, unm1, steps, theta0, newton_iters=4, krylov_iters=15, opts=o)
+    xyz = torch.empty((mesh.n_nodes, 3), dtype=torch.float64, device="cuda")
+    op.node_coords(xyz)
+    x = xyz.cpu().numpy()
+    th = theta0 + steps * omega * dt
+    b = mesh.wall == 2
+    xr = mesh.x0[b, 0] * np.cos(th) - mesh.x0[b, 1] * np.sin(th)
+    yr = mesh.x0[b, 0] * np.sin(th) + mesh.x0[b, 1] * np.cos(th)
+    assert np.abs(x[b, 0] - xr).max() < 1e-12 and np.abs(x[b, 1] - yr).max() < 1e-12
+    u = un.cpu().numpy()
+    err = max(np.abs(u[b, 0] + omega * yr).max(), np.abs(u[b, 1] - omega * xr).max(), np.abs(u[b, 2]).max())
+    assert err < 1e-6 * omega * mesh.R, err
+    assert ke[0] == 0.0 and np.all(ke[1:] > 0.0) and ke[-1] > ke[1], ke
+    assert diss[0] == 0.0 and np.all(diss[1:] > 0.0), diss
+    assert np.all(red[1:] < 1e-5), red
