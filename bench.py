@@ -216,9 +216,9 @@ def transient_leg(args, op, mesh, prm, f, T):
     """BDF2 time steps with the rotor turning at omega (remap every step), each
     step 3 Newton iterations x FGMRES(8) preconditioned by the FP32 multigrid
     V-cycle; the step is captured once as a CUDA graph and replayed.  Reports
-    the time per step (graph vs eager), DoFs/s over the steps, the kinetic
-    energy and viscous dissipation histories and the per-step residual
-    reductions."""
+    the time per step (graph vs eager), DoFs/s over the steps, the histories
+    of kinetic energy, viscous dissipation, impeller torque and wall power,
+    and the per-step residual reductions."""
     import torch
     from paper_2608_27423_b300 import MF_PC_MG, MF_FP32, solver_defaults
     from synth.configs import CONFIGS
@@ -235,16 +235,16 @@ def transient_leg(args, op, mesh, prm, f, T):
         un, unm1 = T(u0), T(u0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ke, diss, red = op.run_transient(un, unm1, args.transient, prm["theta"], newton_iters=3, krylov_iters=8,
-                                         opts=o, use_graph=graph)
+        rec = op.run_transient(un, unm1, args.transient, prm["theta"], newton_iters=3, krylov_iters=8, opts=o,
+                               use_graph=graph)
         torch.cuda.synchronize()
         dt_s = time.perf_counter() - t0
         out[label] = {"seconds": round(dt_s, 4), "ms_per_step": 1e3 * dt_s / args.transient,
                       "dofs_steps_per_s": op.n_dofs * args.transient / dt_s}
         if graph:
-            out["kinetic_energy"] = [float(x) for x in ke]
-            out["viscous_dissipation"] = [float(x) for x in diss]
-            out["residual_reduction_per_step"] = [float(x) for x in red[1:]]
+            for key in ("kinetic_energy", "dissipation_sym", "torque_moving", "power"):
+                out[key] = [float(x) for x in rec[key]]
+            out["residual_reduction_per_step"] = [float(x) for x in rec["residual_reduction"][1:]]
     return out
 
 

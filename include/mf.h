@@ -206,17 +206,42 @@ void mf_solver_defaults(mf_solver_opts* o);
 mf_status mf_solve_step(mf_handle h, double* up, const mf_solver_opts* so, mf_solve_report* rep,
                         void* stream);
 
-/* ---------------------------------------------------------------- transient driver
+/* ---------------------------------------------------------------- energy budget and wall loads
+ * (Section 5.3.2 energy balance, Section 5.2.2 torque analysis)
+ *
  * mf_kinetic_energy: ke_dev (device double) = 1/2 int |u|^2 over the mesh at
  * the current geometry (Gauss rule of the operator); needs the geometry cache
  * of a previous mf_set_linearization.  Asynchronous.
  *
  * mf_energy: the energy budget terms of up at the current geometry, out_dev
- * (device double[2]): out_dev[0] = 1/2 int |u|^2, out_dev[1] = nu int
- * grad u : grad u (the viscous dissipation of the Laplacian form of the
- * viscous term, Eq. 1), Gauss rule of the operator, wall values included.
- * Needs the geometry cache (mf_set_linearization).  Asynchronous.
+ * (device double[3]): [0] 1/2 int |u|^2; [1] nu int grad u : grad u (the
+ * dissipation of the Laplacian form of the viscous term, Eq. 1); [2] nu int
+ * (grad u + grad u^T) : grad u (the paper's -tau : grad u with the deviatoric
+ * stress tau = -nu (grad u + grad u^T)).  Gauss rule of the operator, wall
+ * values included.  Needs the geometry cache.  Asynchronous.
  *
+ * mf_wall_loads: loads the walls exert on the fluid, from the consistent
+ * reactions r = the volume + mortar residual rows of up without the Dirichlet
+ * replacement (on a wall node i, r_i = int_wall t . phi_i with t the wall's
+ * traction on the fluid).  For each group g of wall nodes, out (device
+ * double[n_groups][d+2]): [g][0..d-1] force sum_i r_i, [g][d] torque about
+ * the z axis sum_i (x_i x r_i) . e_z, [g][d+1] power sum_i r_i . u_i.
+ * group: device uint8 [n_nodes], the group of each wall node (values >=
+ * n_groups skipped, non-wall nodes ignored), 1 <= n_groups <= 16; or NULL with
+ * n_groups = 2: group 0 = stationary walls (wall = 1), 1 = walls moving with
+ * the rotor (wall = 2, e.g. the impeller).  The torque the fluid exerts on the
+ * impeller is minus its group's torque, its power number 2 pi T / (N^2 D^5)
+ * (rho = 1).  Uses the history term and angle of the handle; needs the
+ * geometry cache.  The first call allocates an n_dofs scratch vector.
+ * Asynchronous.
+ */
+#define MF_MAX_LOAD_GROUPS 16
+mf_status mf_kinetic_energy(mf_handle h, const double* up, double* ke_dev, void* stream);
+mf_status mf_energy(mf_handle h, const double* up, double* out_dev, void* stream);
+mf_status mf_wall_loads(mf_handle h, const double* up, const uint8_t* group, int n_groups, double* out,
+                        void* stream);
+
+/* ---------------------------------------------------------------- transient driver
  * mf_run_transient: n_steps BDF steps (the handle's dt and BDF order) starting
  * at rotor angle theta0, the rotor advancing by omega*dt per step (rotation and
  * mortar remap every step, Sections 3.1-3.2).  Each step: history term from
@@ -227,16 +252,26 @@ mf_status mf_solve_step(mf_handle h, double* up, const mf_solver_opts* so, mf_so
  * No step waits on the host, so with use_graph = 1 one step is captured as a
  * CUDA graph (on a library stream) and replayed n_steps times on `stream`.
  * u_n, u_nm1: device [n_nodes][d+1] FP64 (u_nm1 unused for BDF1).  On return
- * (synchronising) ke_host[0..n_steps] and diss_host[0..n_steps] hold the
- * kinetic energy and the viscous dissipation (as mf_energy) of the initial
- * state and after each step, red_host[1..n_steps] each step's residual
- * reduction ||R_end|| / ||R_start|| (any of the three may be NULL).  Errors:
+ * (synchronising) rec_host[0..n_steps] (host, may be NULL) holds the record of
+ * the initial state and of each step's solution: energy terms as mf_energy,
+ * wall loads as mf_wall_loads with the default groups (at the step's history
+ * term, so the torque includes the BDF inertia of the wall rows) and the
+ * step's residual reduction ||R_end|| / ||R_start|| (0 in record 0).  The
+ * numerical dissipation of the energy balance follows on the host:
+ * eps_n T-bar = power - dissipation_sym - dE/dt (Section 5.3.2).  Errors:
  * MF_ERR_ARG (dt = 0, counts out of range), MF_ERR_STATE (MG without levels). */
-mf_status mf_kinetic_energy(mf_handle h, const double* up, double* ke_dev, void* stream);
-mf_status mf_energy(mf_handle h, const double* up, double* out_dev, void* stream);
+typedef struct {
+  double kinetic_energy;      /* 1/2 int |u|^2 */
+  double dissipation;         /* nu int grad u : grad u */
+  double dissipation_sym;     /* nu int (grad u + grad u^T) : grad u */
+  double torque_still;        /* z torque of the stationary walls on the fluid */
+  double torque_moving;       /* z torque of the walls moving with the rotor on the fluid */
+  double power;               /* power of all walls on the fluid */
+  double residual_reduction;  /* ||R_end|| / ||R_start|| of the step */
+} mf_step_record;
 mf_status mf_run_transient(mf_handle h, double* u_n, double* u_nm1, int n_steps, double theta0, int newton_iters,
-                           int krylov_iters, const mf_solver_opts* so, int use_graph, double* ke_host,
-                           double* diss_host, double* red_host, void* stream);
+                           int krylov_iters, const mf_solver_opts* so, int use_graph, mf_step_record* rec_host,
+                           void* stream);
 
 /* ---------------------------------------------------------------- no-allocation solve
  * mf_solve_step_static: the same Newton / FGMRES step as mf_solve_step, for

@@ -106,22 +106,26 @@ class Problem:
 
     def energy(self, up):
         """Energy budget terms of the discrete velocity u_h at the current
-        geometry, by the operator's Gauss rule: kinetic energy 1/2 int |u_h|^2
-        and viscous dissipation nu int grad u_h : grad u_h (the dissipation of
-        the Laplacian form of the viscous term in Eq. 1).  Wall values count."""
+        geometry, by the operator's Gauss rule (Section 5.3.2, energy balance):
+        kinetic energy 1/2 int |u_h|^2; viscous dissipation of the Laplacian
+        viscous form, nu int grad u_h : grad u_h; and the paper's dissipation
+        -tau : grad u with the deviatoric stress tau = -nu (grad u + grad u^T),
+        i.e. nu int (grad u_h + grad u_h^T) : grad u_h.  Wall values count."""
         up = np.asarray(up, dtype=np.float64).reshape(self.nn, -1)
         d = self.d
-        ke = diss = 0.0
+        ke = diss = diss_sym = 0.0
         nc = self.cells.shape[0]
         for s0 in range(0, nc, 512):
             cl = np.arange(s0, min(nc, s0 + 512))
             g = self.geometry(cl)
             U = up[self.cells[cl]][..., :d]                              # [C,N,d]
             uq = np.einsum("qa,Kai->Kqi", self.phi, U)
-            gu = np.einsum("Kqam,Kai->Kqim", g["grad"], U)
+            gu = np.einsum("Kqam,Kai->Kqim", g["grad"], U)               # gu[i, m] = d u_i / d x_m
             ke += 0.5 * float((g["W"] * (uq ** 2).sum(-1)).sum())
             diss += self.nu * float((g["W"] * (gu ** 2).sum((-1, -2))).sum())
-        return ke, diss
+            sym = gu + np.swapaxes(gu, -1, -2)
+            diss_sym += self.nu * float((g["W"] * (sym * gu).sum((-1, -2))).sum())
+        return ke, diss, diss_sym
 
     def cell_size(self, cl):
         """h = diameter of the area- (2D) / volume- (3D) equivalent circle/sphere

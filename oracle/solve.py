@@ -1,8 +1,10 @@
 """Global operator with constraints, assembly, and reference solvers (FP64).
 
-* Constraints: homogeneous Dirichlet velocity on walls; constrained rows and
-  columns of the Jacobian become identity (source entries zeroed, result equal
-  to the source there), and the residual there is u - g (g = 0).
+* Constraints: Dirichlet velocity on walls; constrained rows and columns of
+  the Jacobian become identity (source entries zeroed, result equal to the
+  source there), and the residual there is u - g (g given on stationary walls,
+  zero by default; omega e_z x x on walls moving with the rotor).
+* Wall loads (force, torque, power) from the consistent reactions.
 * Assembly (path A): element matrices of the volume terms and of every mortar
   cell pair, scattered into a CSR matrix.
 * Newton (Eq. Eq-Newton-method) with GMRES (Section 4 uses GMRES) on the
@@ -65,6 +67,34 @@ class Operator:
         gg[:, :self.d] = self.g
         r[self.cmask] = up[self.cmask] - gg[self.cmask]
         return r
+
+    def wall_loads(self, up, group=None, n_groups=2):
+        """Loads of the walls on the fluid from the consistent reactions
+        (torque at the impeller, Section 5.2.2; power at the wall in the
+        energy balance, Section 5.3.2).  r = the residual rows of the volume and
+        mortar terms without the Dirichlet replacement; on a wall node i it
+        equals int_wall t . phi_i, t the traction the wall exerts on the fluid.
+        Summed over a group of wall nodes: force sum_i r_i, torque about the
+        z axis sum_i (x_i x r_i) . e_z (= int x x t since sum_i x_i phi_i = x,
+        isoparametric), power sum_i r_i . u_i.  group: [N_n] ints (wall nodes
+        whose group is >= n_groups are skipped); None groups by wall type
+        (0 = stationary, 1 = moving with the rotor).  Returns [n_groups, d+2]:
+        force (d), torque, power."""
+        up = np.asarray(up, dtype=np.float64).reshape(self.nn, self.d + 1)
+        d = self.d
+        r = self.prob.volume_residual(up)
+        self.mortar.apply(up, out=r)
+        x = self.prob.x
+        w = np.asarray(self.prob.mesh.wall)
+        grp = (w.astype(np.int64) - 1) if group is None else np.asarray(group, dtype=np.int64)
+        out = np.zeros((n_groups, d + 2))
+        for gi in range(n_groups):
+            sel = (w > 0) & (grp == gi)
+            rs = r[sel, :d]
+            out[gi, :d] = rs.sum(0)
+            out[gi, d] = float((x[sel, 0] * rs[:, 1] - x[sel, 1] * rs[:, 0]).sum())
+            out[gi, d + 1] = float((rs * up[sel, :d]).sum())
+        return out
 
     def assemble(self):
         """CSR Jacobian (path A): element matrices + mortar pair matrices, then

@@ -161,23 +161,29 @@ class RotorStatorOperator:
         self._chk(self.lib.mf_kinetic_energy(self.h, _ptr(up), _ptr(out), _stream(stream)), "mf_kinetic_energy")
 
     def energy(self, up, out, stream=None):
-        """out (2-element device FP64 tensor) = (1/2 int |u|^2, nu int grad u : grad u)."""
+        """out (3-element device FP64 tensor) = (1/2 int |u|^2, nu int grad u : grad u,
+        nu int (grad u + grad u^T) : grad u)."""
         self._chk(self.lib.mf_energy(self.h, _ptr(up), _ptr(out), _stream(stream)), "mf_energy")
+
+    def wall_loads(self, up, out, group=None, n_groups=2, stream=None):
+        """out (device FP64 [n_groups, d+2]) = per wall group: force on the fluid (d),
+        torque about e_z, power (see mf_wall_loads).  group: device uint8 [n_nodes]
+        or None (0 = stationary walls, 1 = walls moving with the rotor)."""
+        self._chk(self.lib.mf_wall_loads(self.h, _ptr(up), _ptr(group) if group is not None else None,
+                                         int(n_groups), _ptr(out), _stream(stream)), "mf_wall_loads")
 
     def run_transient(self, u_n, u_nm1, n_steps, theta0, newton_iters=3, krylov_iters=6, opts=None,
                       use_graph=True, stream=None):
         """n_steps BDF steps with the rotor turning (see mf_run_transient); returns
-        (kinetic energies, viscous dissipations, residual reductions), each [n_steps+1]."""
-        ke = np.zeros(n_steps + 1)
-        diss = np.zeros(n_steps + 1)
-        red = np.zeros(n_steps + 1)
+        {field: array [n_steps+1]} for the fields of mf_step_record (record 0 is the
+        initial state)."""
+        recs = (_lib.MfStepRecord * (n_steps + 1))()
         o = opts if opts is not None else solver_defaults()
         st = self.lib.mf_run_transient(self.h, _ptr(u_n), _ptr(u_nm1) if u_nm1 is not None else None, int(n_steps),
                                        float(theta0), int(newton_iters), int(krylov_iters), C.byref(o),
-                                       int(bool(use_graph)), _np_ptr(ke), _np_ptr(diss), _np_ptr(red),
-                                       _stream(stream))
+                                       int(bool(use_graph)), recs, _stream(stream))
         self._chk(st, "mf_run_transient")
-        return ke, diss, red
+        return {f: np.array([getattr(r, f) for r in recs]) for f in _lib.STEP_RECORD_FIELDS}
 
     def last_error(self):
         return self.lib.mf_last_error(self.h).decode()

@@ -20,7 +20,7 @@ EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_create", "mf_destroy", "mf
            "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step",
            "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
            "mf_mg_interpolate", "mf_solve_step_static", "mf_batch_create", "mf_batch_destroy",
-           "mf_batch_apply_jacobian", "mf_kinetic_energy", "mf_energy", "mf_run_transient"]
+           "mf_batch_apply_jacobian", "mf_kinetic_energy", "mf_energy", "mf_wall_loads", "mf_run_transient"]
 PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
               "cell_linearization", "dirichlet", "diagonal"]
 
@@ -42,6 +42,14 @@ class MfSolveReport(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("lin_iters_total", C.c_int), ("lin_iters", C.c_int * 64),
                 ("res_norm", C.c_double * 65), ("lambda_max", C.c_double), ("seconds", C.c_double),
                 ("status", C.c_int)]
+
+
+STEP_RECORD_FIELDS = ("kinetic_energy", "dissipation", "dissipation_sym", "torque_still", "torque_moving", "power",
+                      "residual_reduction")
+
+
+class MfStepRecord(C.Structure):
+    _fields_ = [(f, C.c_double) for f in STEP_RECORD_FIELDS]
 
 
 class MfProfile(C.Structure):
@@ -86,7 +94,9 @@ def load():
     lib.mf_solve_step.argtypes = [vp, vp, C.POINTER(MfSolverOpts), C.POINTER(MfSolveReport), vp]
     lib.mf_kinetic_energy.argtypes = [vp, vp, vp, vp]
     lib.mf_energy.argtypes = [vp, vp, vp, vp]
-    lib.mf_run_transient.argtypes = [vp, vp, vp, i32, dbl, i32, i32, C.POINTER(MfSolverOpts), i32, vp, vp, vp, vp]
+    lib.mf_wall_loads.argtypes = [vp, vp, vp, i32, vp, vp]
+    lib.mf_run_transient.argtypes = [vp, vp, vp, i32, dbl, i32, i32, C.POINTER(MfSolverOpts), i32,
+                                     C.POINTER(MfStepRecord), vp]
     lib.mf_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp)]
     lib.mf_batch_destroy.argtypes = [vp]
     lib.mf_batch_apply_jacobian.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), i32, vp]

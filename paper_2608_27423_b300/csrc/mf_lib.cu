@@ -59,9 +59,7 @@ struct Workspace {
   int mi32 = 0, mi64 = 0;    // inner GMRES dimensions allocated
   int part_cap = 0;          // rows of the partial-sum buffer
   double* hout = nullptr;    // transient driver: outer Hessenberg columns and scalars (65536 doubles)
-  double* rec_ke = nullptr;  // per-step kinetic energy record
-  double* rec_diss = nullptr;  // per-step viscous dissipation record
-  double* rec_red = nullptr; // per-step residual reduction record
+  double* rec = nullptr;     // per-step records (mf_step_record layout)
   int* rec_count = nullptr;
   int rec_cap = 0;
   float* f_Vin = nullptr;    // [(mi+1) n] inner FP32 Krylov basis
@@ -114,6 +112,7 @@ struct mf_ctx {
   df* cachedf = nullptr;
   bool df_valid = false;
   double *ht = nullptr, *g = nullptr;
+  double* react = nullptr;             // reaction rows scratch of mf_wall_loads [n_dofs]
   double* cache64 = nullptr;
   float* cache32 = nullptr;
   Workspace ws;
@@ -298,7 +297,7 @@ extern "C" void mf_mesh_free(mf_mesh* m) { delete m; }
 static void free_ws(Workspace& w) {
   void* ptrs[] = {w.V, w.Z, w.w, w.r, w.dx, w.hcol, w.part, w.diag64, w.dinv64, w.dinv32, w.f_v, w.f_x, w.f_r,
                   w.f_d, w.f_t, w.f_w, w.c_x, w.c_r, w.c_d, w.c_t, w.c_v, w.c_w, w.utrial, w.f_Vin, w.c_Vin, w.hin, w.ep, w.jep,
-                  w.hout, w.rec_ke, w.rec_diss, w.rec_red, w.rec_count};
+                  w.hout, w.rec, w.rec_count};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (w.pinned) cudaFreeHost(w.pinned);
   w = Workspace();
@@ -313,7 +312,7 @@ extern "C" mf_status mf_destroy(mf_handle h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
                   h->mc_cell, h->mc_tau, h->mc_xi, h->mc_ang, h->mc_w, h->ht, h->g, h->cache64, h->cache32,
-                  h->mg_jinv64, h->mg_jinv32, h->mg_jinvdf, h->cachedf, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32};
+                  h->mg_jinv64, h->mg_jinv32, h->mg_jinvdf, h->cachedf, h->react, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32};
   for (void* p : ptrs) if (p) cudaFree(p);
   free_ws(h->ws);
   delete h;
@@ -462,12 +461,18 @@ extern "C" mf_status mf_set_linearization(mf_handle h, const double* up_star, do
   return MF_OK;
 }
 
-extern "C" mf_status mf_residual(mf_handle h, const double* up, double* r, void* stream) {
-  if (!h || !up || !r) return MF_ERR_ARG;
-  cudaStream_t st = S(stream);
+// Volume + mortar residual rows without the Dirichlet replacement (on wall
+// nodes these are the consistent reactions).
+static mf_status residual_rows(mf_ctx* h, const double* up, double* r, cudaStream_t st) {
   CK(cudaMemsetAsync(r, 0, h->ndof * 8, st));
   MF_DISPATCH(h->d, h->k, (launch_state<D, K>(h, 1, up, r, st)));
   MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, double>(h, 0, up, r, 0, st)));
+  CK(cudaGetLastError());
+  return MF_OK;
+}
+
+// r = u - g on the wall velocity rows
+static mf_status residual_constrain(mf_ctx* h, const double* up, double* r, cudaStream_t st) {
   if (h->nwall) {
     const int64_t m0 = h->nwall - h->nmwall;
     if (h->d == 2) k_dirichlet_res<2><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, m0, up, h->g, h->x, h->omega, r);
@@ -475,6 +480,39 @@ extern "C" mf_status mf_residual(mf_handle h, const double* up, double* r, void*
   }
   CK(cudaGetLastError());
   return MF_OK;
+}
+
+extern "C" mf_status mf_residual(mf_handle h, const double* up, double* r, void* stream) {
+  if (!h || !up || !r) return MF_ERR_ARG;
+  cudaStream_t st = S(stream);
+  mf_status e = residual_rows(h, up, r, st);
+  if (e != MF_OK) return e;
+  return residual_constrain(h, up, r, st);
+}
+
+// Wall loads from reaction rows r: out[g][0..d-1] force, [d] torque about e_z,
+// [d+1] power, summed over the wall nodes of group g (zeroed first).
+static mf_status wall_loads_from_rows(mf_ctx* h, const double* up, const double* r, const uint8_t* group, int n_groups,
+                                      double* out, cudaStream_t st) {
+  CK(cudaMemsetAsync(out, 0, sizeof(double) * n_groups * (h->d + 2), st));
+  if (h->nwall) {
+    const int64_t m0 = h->nwall - h->nmwall;
+    const unsigned nb = std::min<unsigned>(nblk(h->nwall, 256), 148 * 2);
+    if (h->d == 2) k_wall_loads<2><<<nb, 256, 0, st>>>(h->wall, h->nwall, m0, group, n_groups, h->x, up, r, out);
+    else k_wall_loads<3><<<nb, 256, 0, st>>>(h->wall, h->nwall, m0, group, n_groups, h->x, up, r, out);
+  }
+  CK(cudaGetLastError());
+  return MF_OK;
+}
+
+extern "C" mf_status mf_wall_loads(mf_handle h, const double* up, const uint8_t* group, int n_groups, double* out,
+                                   void* stream) {
+  if (!h || !up || !out || n_groups < 1 || n_groups > MF_MAX_LOAD_GROUPS || (!group && n_groups != 2)) return MF_ERR_ARG;
+  cudaStream_t st = S(stream);
+  if (!h->react) CK(cudaMalloc((void**)&h->react, h->ndof * sizeof(double)));
+  mf_status e = residual_rows(h, up, h->react, st);
+  if (e != MF_OK) return e;
+  return wall_loads_from_rows(h, up, h->react, group, n_groups, out, st);
 }
 
 template <typename T>

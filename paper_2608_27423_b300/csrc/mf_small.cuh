@@ -45,6 +45,43 @@ __global__ void k_dirichlet_res(const int32_t* __restrict__ wall, int64_t nw, in
 #pragma unroll
   for (int c = 0; c < D; ++c) r[n * (D + 1) + c] = up[n * (D + 1) + c] - gv[c];
 }
+// Wall loads from the reaction rows r (volume + mortar residual without the
+// Dirichlet replacement): per group g, out[g][0..D-1] += r_i (force on the
+// fluid), out[g][D] += (x_i x r_i) . e_z (torque), out[g][D+1] += r_i . u_i
+// (power).  Group of wall-list entry i: group[node] if group is given (values
+// >= n_groups skipped), else 0 for stationary walls (i < m0) and 1 for walls
+// moving with the rotor.  Block partial sums in shared memory, one global
+// atomic per block and value.
+template <int D>
+__global__ void __launch_bounds__(256) k_wall_loads(const int32_t* __restrict__ wall, int64_t nw, int64_t m0,
+                                                    const uint8_t* __restrict__ group, int n_groups,
+                                                    const double* __restrict__ x, const double* __restrict__ up,
+                                                    const double* __restrict__ r, double* __restrict__ out) {
+  constexpr int NV = D + 2;
+  __shared__ double acc[MF_MAX_LOAD_GROUPS * NV];
+  for (int j = threadIdx.x; j < n_groups * NV; j += blockDim.x) acc[j] = 0.0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = wall[i];
+    const int gi = group ? (int)group[n] : (i >= m0 ? 1 : 0);
+    if (gi >= n_groups) continue;
+    double v[NV];
+    double pw = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      v[c] = r[n * (D + 1) + c];
+      pw = fma(v[c], up[n * (D + 1) + c], pw);
+    }
+    v[D] = x[n * D] * v[1] - x[n * D + 1] * v[0];
+    v[D + 1] = pw;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) atomicAdd(&acc[gi * NV + j], v[j]);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n_groups * NV; j += blockDim.x)
+    if (acc[j] != 0.0) atomicAdd(&out[j], acc[j]);
+}
+
 // diag = 1 on wall velocity DoFs.
 template <int D, typename T>
 __global__ void k_dirichlet_one(const int32_t* __restrict__ wall, int64_t nw, T* __restrict__ y) {

@@ -101,16 +101,34 @@ def test_diagonal_matches_assembled(c):
 
 @pytest.mark.parametrize("c", CASES, ids=cid)
 def test_energy_matches_oracle(c):
-    """mf_energy (kinetic energy, viscous dissipation) and mf_kinetic_energy."""
+    """mf_energy (kinetic energy, both dissipation forms) and mf_kinetic_energy."""
     mesh, prm, f, op, g, T = setup(**c)
     up = f["up_star"] * 0.7 + 0.1
-    ke_ref, di_ref = op.prob.energy(up)
-    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    ref = np.array(op.prob.energy(up))
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
     g.energy(T(up), out)
-    ke, di = out.cpu().numpy()
-    assert abs(ke / ke_ref - 1) <= TOL64 and abs(di / di_ref - 1) <= TOL64, (ke, ke_ref, di, di_ref)
+    assert np.abs(out.cpu().numpy() / ref - 1).max() <= TOL64, (out, ref)
     g.kinetic_energy(T(up), out[:1])
-    assert abs(float(out[0]) / ke_ref - 1) <= TOL64
+    assert abs(float(out[0]) / ref[0] - 1) <= TOL64
+
+
+@pytest.mark.parametrize("c", CASES, ids=cid)
+def test_wall_loads_match_oracle(c):
+    """mf_wall_loads: default groups (stationary / moving walls) and caller groups."""
+    mesh, prm, f, op, g, T = setup(**c)
+    up = f["up_star"] * 0.7 + 0.1
+    d = mesh.d
+    out = torch.empty((2, d + 2), dtype=torch.float64, device="cuda")
+    g.wall_loads(T(up), out)
+    ref = op.wall_loads(up)
+    assert rel(out.cpu().numpy(), ref) <= TOL64
+    # three groups by position, one group (7) skipped
+    x = op.prob.x
+    grp = np.where(x[:, 0] > 0, 0, np.where(x[:, 1] > 0, 1, 2)).astype(np.uint8)
+    grp[::7] = 7
+    out3 = torch.empty((3, d + 2), dtype=torch.float64, device="cuda")
+    g.wall_loads(T(up), out3, group=torch.tensor(grp, device="cuda"), n_groups=3)
+    assert rel(out3.cpu().numpy(), op.wall_loads(up, group=grp, n_groups=3)) <= TOL64
 
 
 def test_node_coordinates_follow_rotation():

@@ -103,9 +103,8 @@ def test_transient_driver_graph_replay_equals_eager(pc):
         un, unm1 = T(u0), T(um1)
         o = solver_defaults(pc=MF_PC_MG if pc == "mg" else MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=30,
                             mg_smooth=4, mg_coarse_iters=40)
-        ke, diss, red = ops[0].run_transient(un, unm1, 6, 0.137, newton_iters=4, krylov_iters=15, opts=o,
-                                             use_graph=use_graph)
-        res[use_graph] = (un.cpu().numpy(), ke, red, diss)
+        rec = ops[0].run_transient(un, unm1, 6, 0.137, newton_iters=4, krylov_iters=15, opts=o, use_graph=use_graph)
+        res[use_graph] = (un.cpu().numpy(), rec["kinetic_energy"], rec["residual_reduction"], rec["dissipation"])
     (a, ke_a, red_a, diss_a), (b, ke_b, red_b, diss_b) = res[False], res[True]
     # both runs solve every step to the fixed iteration budget; atomics reorder sums and the FP32
     # inner solves pass those roundoff differences on at the level of the step tolerance.  The
@@ -133,7 +132,8 @@ def test_transient_blades_move_with_the_rotor():
     u0 = np.zeros((mesh.n_nodes, 4))
     un, unm1 = T(u0), T(u0)
     o = solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=30)
-    ke, diss, red = op.run_transient(un, unm1, steps, theta0, newton_iters=4, krylov_iters=15, opts=o)
+    rec = op.run_transient(un, unm1, steps, theta0, newton_iters=4, krylov_iters=15, opts=o)
+    ke, diss, red = rec["kinetic_energy"], rec["dissipation"], rec["residual_reduction"]
     xyz = torch.empty((mesh.n_nodes, 3), dtype=torch.float64, device="cuda")
     op.node_coords(xyz)
     x = xyz.cpu().numpy()
@@ -148,3 +148,12 @@ def test_transient_blades_move_with_the_rotor():
     assert ke[0] == 0.0 and np.all(ke[1:] > 0.0) and ke[-1] > ke[1], ke
     assert diss[0] == 0.0 and np.all(diss[1:] > 0.0), diss
     assert np.all(red[1:] < 1e-5), red
+    # the blades drive the fluid: positive torque and power on the fluid; the recorded
+    # loads of the last step equal mf_wall_loads on its solution (same history, angle)
+    assert np.all(rec["torque_moving"][1:] > 0.0) and np.all(rec["power"][1:] > 0.0), rec
+    out = torch.empty((2, 5), dtype=torch.float64, device="cuda")
+    op.wall_loads(un, out)
+    lo = out.cpu().numpy()
+    assert abs(lo[1, 3] / rec["torque_moving"][-1] - 1) < 1e-12 and abs(lo[0, 3] - rec["torque_still"][-1]) < \
+        1e-12 * abs(lo[1, 3])
+    assert abs(lo[:, 4].sum() / rec["power"][-1] - 1) < 1e-12
