@@ -141,7 +141,8 @@ def aggregate_ranks(ms_local, dofs_local, dist=None, device=None):
 # --------------------------------------------------------------------- solve leg
 def build_levels(op, cfg, prm, n_h):
     """Multigrid levels below `op`: one polynomial level (k -> k-1) when k >= 3,
-    then geometric halvings of the mesh (n_h levels in all below the finest)."""
+    then geometric halvings of the mesh (n_h levels in all below the finest).
+    cfg: the mesh parameters d, k, m, n_r, n_s, n_z of `op`."""
     from paper_2608_27423_b300 import RotorStatorOperator
     base = dict(d=cfg["d"], k=cfg["k"], m=cfg["m"], n_r=cfg["n_r"], n_s=cfg["n_s"], n_z=cfg["n_z"])
     levels = [op]
@@ -256,21 +257,29 @@ def batched_leg(args, T, dev):
     """12 independent cylinders (Re in BATCH_RE, omega = 1, Q2, BDF2 dt = 0.005,
     rotor angle 0.137 i, m = 16 .. 32 -> ~16k .. ~131k hexes): FP64 Jacobian
     applies of all instances, one persistent launch per kernel kind against
-    the instances applied one after another."""
+    the instances applied one after another; then one nonlinear step of all
+    12 to ||R|| <= 1e-8 ||R_0|| (mf_batch_solve_step: Newton with FGMRES(8),
+    FP64 outer applies, FP32 multigrid V-cycle per instance, one Newton
+    iteration of the batch as a CUDA graph), batched against sequential."""
     import torch
     from paper_2608_27423_b300 import RotorStatorOperator, BatchedOperators
-    ops, xs = [], []
+    ops, xs, cfgs, fields, meshes, prms = [], [], [], [], [], []
     for i, re in enumerate(BATCH_RE):
         m = 16 + (16 * i) // 11
         m -= m % 2
         nu = 1.0 / (2.0 * np.pi * re)
-        mesh, prm, f = synth.make_config(d=3, k=2, m=m, n_r=max(2, m // 4), n_s=m // 2, n_z=m, nu=nu, omega=1.0,
-                                         dt=0.005, bdf=2, theta=0.137 * i, state="smooth", seed=20260 + 10 * i)
+        cfg = dict(d=3, k=2, m=m, n_r=max(2, m // 4), n_s=m // 2, n_z=m)
+        mesh, prm, f = synth.make_config(**cfg, nu=nu, omega=1.0, dt=0.005, bdf=2, theta=0.137 * i, state="smooth",
+                                         seed=20260 + 10 * i)
         op = RotorStatorOperator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
         op.set_history(T(f["u_n"]), T(f["u_nm1"]))
         op.set_linearization(T(f["up_star"]), prm["theta"])
         ops.append(op)
         xs.append(T(f["x"]))
+        cfgs.append(cfg)
+        fields.append(f)
+        meshes.append(mesh)
+        prms.append(prm)
     ys = [torch.empty_like(x) for x in xs]
     batch = BatchedOperators(ops)
     stream = torch.cuda.current_stream()
@@ -294,9 +303,42 @@ def batched_leg(args, T, dev):
     ms_seq = run(seq)
     ms_bat = run(lambda: batch.apply_jacobian(xs, ys))
     dofs = sum(op.n_dofs for op in ops)
-    return {"instances": len(ops), "cells": [op.n_cells for op in ops], "total_dofs": dofs,
-            "ms_one_by_one": ms_seq, "ms_batched": ms_bat, "dofs_per_s_batched": dofs / (ms_bat * 1e-3),
-            "speedup": ms_seq / ms_bat}
+    out = {"instances": len(ops), "cells": [op.n_cells for op in ops], "total_dofs": dofs,
+           "ms_one_by_one": ms_seq, "ms_batched": ms_bat, "dofs_per_s_batched": dofs / (ms_bat * 1e-3),
+           "speedup": ms_seq / ms_bat}
+    if args.no_solve:
+        return out
+    # ---- one nonlinear step of all instances
+    from paper_2608_27423_b300 import MF_PC_MG, MF_FP32, solver_defaults
+    for op, cfg, prm in zip(ops, cfgs, prms):
+        build_levels(op, cfg, prm, args.mg_levels - 1)
+    u0s = []
+    for mesh, f in zip(meshes, fields):
+        u0 = np.zeros_like(f["up_star"])
+        u0[:, :3] = f["u_n"]
+        u0[mesh.wall.astype(bool), :3] = 0.0
+        u0s.append(u0)
+    o = solver_defaults(pc=MF_PC_MG, pc_precision=MF_FP32, newton_rtol=1e-8, max_newton=20, mg_smooth=4,
+                        mg_coarse_iters=40)
+    thetas = [p["theta"] for p in prms]
+    sols = {}
+    for label, batched in (("batched", True), ("one_by_one", False)):
+        ups = [T(u) for u in u0s]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, reps = batch.solve_step(ups, thetas, o, krylov_iters=8, batched=batched, use_graph=True)
+        torch.cuda.synchronize()
+        dt_s = time.perf_counter() - t0
+        it = reps[0].newton_iters
+        out[f"solve_{label}"] = {"status": int(st), "seconds": round(dt_s, 4), "newton_iters": it,
+                                 "fgmres_per_newton": 8,
+                                 "max_res_reduction": max(r.res_norm[it] / r.res_norm[0] for r in reps)}
+        print(f"batched solve {label}: status {st} {dt_s:.2f}s newton {it}", file=sys.stderr, flush=True)
+        sols[label] = ups
+    out["solve_speedup"] = out["solve_one_by_one"]["seconds"] / out["solve_batched"]["seconds"]
+    out["solve_max_rel_diff"] = max(float((a[:, :3] - b[:, :3]).norm() / b[:, :3].norm())
+                                    for a, b in zip(sols["batched"], sols["one_by_one"]))
+    return out
 
 
 # --------------------------------------------------------------------- CPU oracle

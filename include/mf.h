@@ -93,6 +93,49 @@ mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const double* x0,
                               mf_mesh** out);
 void mf_mesh_free(mf_mesh* m);
 
+/* mf_mesh_rotor_stator: generate a merged rotor-stator mesh (Section 3.1: the
+ * two grids are built separately and meet on a circle of radius R that both
+ * split into n_R = 4 m equal cells).
+ *   rotor disk r < R: O-grid of an m x m centre square of half width sq * R and
+ *     four ring blocks of m x n_r cells blending the square's sides into the
+ *     circle; stator annulus R < r < R_out: n_R x n_s polar cells;
+ *   d = 3: both extruded in n_z layers over [0, H]; blades > 0 marks that many
+ *     equally spaced radial blades in the rotor (the ring cells of one angular
+ *     index, inner three quarters of the rings, middle half of the height) as
+ *     walls moving with the rotor (wall = 2).
+ * Q_k nodes at the Gauss-Lobatto points of each cell's parameter square, on the
+ * blocks' parametric maps (interface nodes exactly on the circle, duplicated
+ * per side); cell-local nodes in tensor order, xi_0 fastest; ring and stator
+ * cells xi_0 radial outward, xi_1 counter-clockwise.  Walls: r = R_out (and
+ * z = 0, H).  The interface cell tables follow mf_mesh_from_arrays.  Errors:
+ * MF_ERR_ARG for out-of-range parameters (d, k in 1..5, m, n_r, n_s, n_z >= 1,
+ * 0 < R < R_out, H > 0, 0 < sq < 1/sqrt 2, blades in 0..n_R and only in 3D) or
+ * more than 2^31 - 1 nodes.
+ * mf_mesh_params_defaults: d 3, k 2, m 8, n_r 2, n_s 4, n_z 8, R 0.5, R_out 1,
+ * H 1, sq 0.55, phi0 -pi/4, no blades.
+ * mf_mesh_sizes / mf_mesh_read: the mesh's sizes and a copy of its arrays into
+ * caller HOST buffers sized as in mf_mesh_from_arrays (any pointer may be NULL).
+ * mf_mesh_coarsen_map: the parameters of the uniformly coarsened mesh (every
+ * block halved along each cell direction; m, n_r, n_s and in 3D n_z must be
+ * even, else MF_ERR_ARG) and, when parent / child are not NULL (host, one entry
+ * per fine cell), the coarse cell containing each fine cell and its child code
+ * (bit r set when the fine cell is the upper half along xi_r), the inputs of
+ * mf_mg_attach for the geometric levels of the multigrid (Section 3.4). */
+typedef struct {
+  int    d, k;
+  int    m, n_r, n_s, n_z;
+  double R, R_out, H;
+  double sq;
+  double phi0;
+  int    blades;
+} mf_mesh_params;
+void mf_mesh_params_defaults(mf_mesh_params* p);
+mf_status mf_mesh_rotor_stator(const mf_mesh_params* p, mf_mesh** out);
+mf_status mf_mesh_sizes(const mf_mesh* m, int* d, int* k, int64_t* n_nodes, int64_t* n_cells, int* n_R, int* n_z);
+mf_status mf_mesh_read(const mf_mesh* m, double* x0, uint8_t* node_side, uint8_t* wall, int32_t* cells,
+                       uint8_t* cell_side, int32_t* iface_rotor, int32_t* iface_stator);
+mf_status mf_mesh_coarsen_map(const mf_mesh_params* fine, mf_mesh_params* coarse, int32_t* parent, uint8_t* child);
+
 /* ---------------------------------------------------------------- options */
 typedef struct {
   double penalty_F;   /* F of Eq. EqPenalty (default 1) */
@@ -318,6 +361,64 @@ mf_status mf_batch_create(const mf_handle* hs, int n, mf_batch** out);
 mf_status mf_batch_destroy(mf_batch* b);
 mf_status mf_batch_apply_jacobian(mf_batch* b, const void* const* xs, void* const* ys, mf_precision prec,
                                   void* stream);
+
+/* mf_batch_solve_step: one nonlinear step (Eq. Eq-Newton-method) of every
+ * instance of the batch, each at its own rotor angle thetas[i] (host array)
+ * from the initial guess ups[i] (HOST array of n device pointers,
+ * [n_nodes_i][d+1] FP64, overwritten by the result).  Each Newton iteration
+ * of each instance: linearisation at its iterate (Section 2.3 blocks, frozen
+ * tau), Jacobi diagonal (Algorithm 1) in so->pc_precision, multigrid levels
+ * for MF_PC_MG (attached with mf_mg_attach), rhs = -R, then FGMRES with a
+ * fixed dimension krylov_iters (1..100; CGS2, right preconditioned by so->pc
+ * = MF_PC_JACOBI, MF_PC_GMRES or MF_PC_MG; least squares on the device) and
+ * a full Newton step.  The outer FGMRES and its Jacobian applies are FP64.
+ *   batched = 1: the per-instance work runs on streams forked from `stream`
+ *                and the outer Jacobian applies of all instances run as one
+ *                persistent launch per kernel kind (one tile queue);
+ *   batched = 0: the instances run one after another on `stream`, each with
+ *                its own applies (same arithmetic).
+ *   use_graph = 1: one Newton iteration of the whole batch is captured as a
+ *                CUDA graph (once per call) and replayed.
+ * After each iteration the host reads the n residual norms back (one small
+ * copy and a synchronisation) and stops when every instance has ||R_i|| <=
+ * newton_rtol ||R_i,0|| or <= newton_atol, or after so->max_newton (<= 64)
+ * iterations; every instance takes every iteration.  reps (host, n entries,
+ * may be NULL): res_norm[0..newton_iters], lin_iters, wall seconds of the
+ * call, status.  Returns MF_OK when every instance converged, otherwise the
+ * first failing instance's status (MF_ERR_NOT_CONVERGED or MF_ERR_NAN; ups
+ * then hold the last iterates).  Errors: MF_ERR_ARG (null pointers,
+ * non-finite angle, pc = MF_PC_CHEBYSHEV, outer_precision != MF_FP64),
+ * MF_ERR_STATE (profiling on, MF_PC_MG without levels).  Synchronising.
+ * Not part of the paper, which solves one problem at a time. */
+mf_status mf_batch_solve_step(mf_batch* b, double* const* ups, const double* thetas, const mf_solver_opts* so,
+                              int krylov_iters, int batched, int use_graph, mf_solve_report* reps, void* stream);
+const char* mf_batch_last_error(mf_batch* b);
+
+/* ---------------------------------------------------------------- launch-shape autotuning
+ * The cell Jacobian kernel runs one thread per Gauss point and several cells
+ * per block; the 3D Q2 and Q3 kernels are compiled for three cells-per-block
+ * values (Q2: 9 (default), 4, 16; Q3: 4 (default), 2, 6), other (d, k) for the
+ * default only.  mf_autotune times every variant of the FP64 and of the FP32
+ * kernel on this handle's mesh and current linearisation (CUDA events, 3
+ * warm-up and 20 timed launches each, on `stream`) and keeps the fastest for
+ * this handle's later applies.  res (host, may be NULL) receives two entries,
+ * [0] FP64 and [1] FP32.  cache_path (may be NULL): a text file of earlier
+ * choices, one line "<gpu name> <d> <k> <n_cells> <64|32> <cells per block>";
+ * a matching line is used without timing (from_cache = 1), a new choice is
+ * appended.  Needs a linearisation (MF_ERR_STATE otherwise); allocates two
+ * temporary vectors; synchronising.  The double-float apply keeps the default.
+ * mf_set_cells_per_block forces a variant (cpb = 0: the default); MF_ERR_ARG
+ * when no variant with cpb cells per block is compiled for the handle's d, k.
+ * Not in the paper (its CPU code vectorises over cell batches instead). */
+typedef struct {
+  int    n_variants;          /* variants timed (1 when d, k has only the default) */
+  int    cells_per_block[3];
+  double ms[3];               /* mean kernel time per launch (0 when read from the cache) */
+  int    chosen;              /* index into cells_per_block */
+  int    from_cache;
+} mf_tune_result;
+mf_status mf_autotune(mf_handle h, const char* cache_path, mf_tune_result* res, void* stream);
+mf_status mf_set_cells_per_block(mf_handle h, mf_precision prec, int cpb);
 
 /* ---------------------------------------------------------------- multigrid
  * The global-coarsening multigrid of Section 3.4 (geometric and polynomial

@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import MF_FP64, MF_FP32, MF_DF64, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
     MfSolverOpts, MfSolveReport
 
-__all__ = ["RotorStatorOperator", "BatchedOperators", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
+__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
            "solver_defaults"]
 
 
@@ -46,6 +46,81 @@ def solver_defaults(**over):
     for k, v in over.items():
         setattr(o, k, v)
     return o
+
+
+class Mesh:
+    """A rotor-stator mesh generated by the library (mf_mesh_rotor_stator), as
+    host arrays: x0 [N_n, d], cells [N_c, (k+1)^d] int32, cell_side,
+    node_side, wall (uint8), iface_rotor / iface_stator [n_z, n_R] int32,
+    and R, n_R, n_z, H, phi0; `params` holds the generator parameters."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+    @property
+    def n_nodes(self):
+        return self.x0.shape[0]
+
+    @property
+    def n_cells(self):
+        return self.cells.shape[0]
+
+    @property
+    def n_dofs(self):
+        return self.n_nodes * (self.d + 1)
+
+
+def _mesh_params(params):
+    p = _lib.MfMeshParams()
+    _lib.load().mf_mesh_params_defaults(C.byref(p))
+    for key, v in params.items():
+        if key not in dict(_lib.MfMeshParams._fields_):
+            raise TypeError(f"unknown mesh parameter {key}")
+        setattr(p, key, v)
+    return p
+
+
+def rotor_stator_mesh(**params):
+    """Generate a rotor-stator mesh in the library (parameters of
+    mf_mesh_params: d, k, m, n_r, n_s, n_z, R, R_out, H, sq, phi0, blades;
+    the rest default) and return it as a Mesh."""
+    lib = _lib.load()
+    p = _mesh_params(params)
+    mp = C.c_void_p()
+    _check(lib.mf_mesh_rotor_stator(C.byref(p), C.byref(mp)), None, "mf_mesh_rotor_stator")
+    try:
+        d, k, n_R, n_z = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        nn, nc = C.c_int64(), C.c_int64()
+        _check(lib.mf_mesh_sizes(mp, C.byref(d), C.byref(k), C.byref(nn), C.byref(nc), C.byref(n_R), C.byref(n_z)),
+               None, "mf_mesh_sizes")
+        d, k, nn, nc, n_R, n_z = d.value, k.value, nn.value, nc.value, n_R.value, n_z.value
+        x0 = np.empty((nn, d))
+        ns, wall = np.empty(nn, np.uint8), np.empty(nn, np.uint8)
+        cells = np.empty((nc, (k + 1) ** d), np.int32)
+        cs = np.empty(nc, np.uint8)
+        ifr, ifs = np.empty((n_z, n_R), np.int32), np.empty((n_z, n_R), np.int32)
+        _check(lib.mf_mesh_read(mp, _np_ptr(x0), _np_ptr(ns), _np_ptr(wall), _np_ptr(cells), _np_ptr(cs),
+                                _np_ptr(ifr), _np_ptr(ifs)), None, "mf_mesh_read")
+    finally:
+        lib.mf_mesh_free(mp)
+    pd = {f: getattr(p, f) for f, _ in _lib.MfMeshParams._fields_}
+    return Mesh(d=d, k=k, x0=x0, cells=cells, cell_side=cs, node_side=ns, wall=wall, iface_rotor=ifr,
+                iface_stator=ifs, R=p.R, n_R=n_R, n_z=n_z, H=(p.H if d == 3 else 1.0), phi0=p.phi0, params=pd)
+
+
+def coarsen_map(**params):
+    """Uniform coarsening of a generated mesh (mf_mesh_coarsen_map): returns
+    (coarse parameters as a dict, parent [N_c] int32, child [N_c] uint8) for
+    RotorStatorOperator.mg_attach."""
+    lib = _lib.load()
+    p = _mesh_params(params)
+    fine = rotor_stator_mesh(**params)
+    cp = _lib.MfMeshParams()
+    parent = np.empty(fine.n_cells, np.int32)
+    child = np.empty(fine.n_cells, np.uint8)
+    _check(lib.mf_mesh_coarsen_map(C.byref(p), C.byref(cp), _np_ptr(parent), _np_ptr(child)), None,
+           "mf_mesh_coarsen_map")
+    return {f: getattr(cp, f) for f, _ in _lib.MfMeshParams._fields_}, parent, child
 
 
 class RotorStatorOperator:
@@ -188,6 +263,23 @@ class RotorStatorOperator:
     def last_error(self):
         return self.lib.mf_last_error(self.h).decode()
 
+    def autotune(self, cache_path=None, stream=None):
+        """Time the cells-per-block variants of the FP64 and FP32 cell Jacobian
+        kernels (mf_autotune) and keep the fastest.  Returns one dict per
+        precision: variants, ms, chosen cells per block, from_cache."""
+        res = (_lib.MfTuneResult * 2)()
+        cp = cache_path.encode() if cache_path else None
+        self._chk(self.lib.mf_autotune(self.h, cp, res, _stream(stream)), "mf_autotune")
+        out = {}
+        for name, r in zip(("fp64", "fp32"), res):
+            n = r.n_variants
+            out[name] = {"cells_per_block": list(r.cells_per_block[:n]), "ms": list(r.ms[:n]),
+                         "chosen": r.cells_per_block[r.chosen], "from_cache": bool(r.from_cache)}
+        return out
+
+    def set_cells_per_block(self, prec, cpb):
+        self._chk(self.lib.mf_set_cells_per_block(self.h, int(prec), int(cpb)), "mf_set_cells_per_block")
+
     def solve_step(self, up, opts=None, stream=None):
         rep = MfSolveReport()
         o = opts if opts is not None else solver_defaults()
@@ -214,6 +306,23 @@ class BatchedOperators:
         ya = (C.c_void_p * n)(*[y.data_ptr() for y in ys])
         st = self.lib.mf_batch_apply_jacobian(self.b, xa, ya, int(prec), _stream(stream))
         _check(st, None, "mf_batch_apply_jacobian")
+
+    def solve_step(self, ups, thetas, opts=None, krylov_iters=8, batched=True, use_graph=True, stream=None):
+        """One Newton step of every instance (mf_batch_solve_step); ups are
+        overwritten.  Returns (status, [MfSolveReport per instance])."""
+        n = len(self.ops)
+        ua = (C.c_void_p * n)(*[u.data_ptr() for u in ups])
+        ta = (C.c_double * n)(*[float(t) for t in thetas])
+        reps = (MfSolveReport * n)()
+        o = opts if opts is not None else solver_defaults()
+        st = self.lib.mf_batch_solve_step(self.b, ua, ta, C.byref(o), int(krylov_iters), int(bool(batched)),
+                                          int(bool(use_graph)), reps, _stream(stream))
+        if st not in (_lib.MF_OK, _lib.MF_ERR_NOT_CONVERGED, _lib.MF_ERR_NAN):
+            raise MfError(f"mf_batch_solve_step: {_lib.STATUS_NAMES[st]} ({self.last_error()})")
+        return st, list(reps)
+
+    def last_error(self):
+        return self.lib.mf_batch_last_error(self.b).decode()
 
     def close(self):
         if getattr(self, "b", None):

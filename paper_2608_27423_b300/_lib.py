@@ -15,14 +15,21 @@ MF_FP64, MF_FP32, MF_DF64 = 0, 1, 2
 MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG = 0, 1, 2, 3
 
 # every symbol include/mf.h declares
-EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_create", "mf_destroy", "mf_last_error", "mf_sizes",
+EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_mesh_params_defaults", "mf_mesh_rotor_stator", "mf_mesh_sizes",
+           "mf_mesh_read", "mf_mesh_coarsen_map", "mf_create", "mf_destroy", "mf_last_error", "mf_sizes",
            "mf_set_angle", "mf_node_coords", "mf_dirichlet", "mf_set_history", "mf_set_linearization",
            "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step",
            "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
            "mf_mg_interpolate", "mf_solve_step_static", "mf_batch_create", "mf_batch_destroy",
-           "mf_batch_apply_jacobian", "mf_kinetic_energy", "mf_energy", "mf_wall_loads", "mf_run_transient"]
+           "mf_batch_apply_jacobian", "mf_batch_solve_step", "mf_batch_last_error", "mf_autotune", "mf_set_cells_per_block", "mf_kinetic_energy", "mf_energy", "mf_wall_loads", "mf_run_transient"]
 PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
               "cell_linearization", "dirichlet", "diagonal"]
+
+
+class MfMeshParams(C.Structure):
+    _fields_ = [("d", C.c_int), ("k", C.c_int), ("m", C.c_int), ("n_r", C.c_int), ("n_s", C.c_int),
+                ("n_z", C.c_int), ("R", C.c_double), ("R_out", C.c_double), ("H", C.c_double), ("sq", C.c_double),
+                ("phi0", C.c_double), ("blades", C.c_int)]
 
 
 class MfOptions(C.Structure):
@@ -52,6 +59,11 @@ class MfStepRecord(C.Structure):
     _fields_ = [(f, C.c_double) for f in STEP_RECORD_FIELDS]
 
 
+class MfTuneResult(C.Structure):
+    _fields_ = [("n_variants", C.c_int), ("cells_per_block", C.c_int * 3), ("ms", C.c_double * 3),
+                ("chosen", C.c_int), ("from_cache", C.c_int)]
+
+
 class MfProfile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
 
@@ -76,6 +88,13 @@ def load():
                                         C.POINTER(vp)]
     lib.mf_mesh_free.argtypes = [vp]
     lib.mf_mesh_free.restype = None
+    lib.mf_mesh_params_defaults.argtypes = [C.POINTER(MfMeshParams)]
+    lib.mf_mesh_params_defaults.restype = None
+    lib.mf_mesh_rotor_stator.argtypes = [C.POINTER(MfMeshParams), C.POINTER(vp)]
+    lib.mf_mesh_sizes.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
+                                  C.POINTER(i32)]
+    lib.mf_mesh_read.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.mf_mesh_coarsen_map.argtypes = [C.POINTER(MfMeshParams), C.POINTER(MfMeshParams), vp, vp]
     lib.mf_create.argtypes = [vp, i32, dbl, dbl, dbl, i32, vp, C.POINTER(vp)]
     lib.mf_destroy.argtypes = [vp]
     lib.mf_last_error.argtypes = [vp]
@@ -100,6 +119,12 @@ def load():
     lib.mf_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp)]
     lib.mf_batch_destroy.argtypes = [vp]
     lib.mf_batch_apply_jacobian.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), i32, vp]
+    lib.mf_batch_solve_step.argtypes = [vp, C.POINTER(vp), C.POINTER(dbl), C.POINTER(MfSolverOpts), i32, i32, i32,
+                                        C.POINTER(MfSolveReport), vp]
+    lib.mf_autotune.argtypes = [vp, C.c_char_p, C.POINTER(MfTuneResult), vp]
+    lib.mf_set_cells_per_block.argtypes = [vp, i32, i32]
+    lib.mf_batch_last_error.argtypes = [vp]
+    lib.mf_batch_last_error.restype = C.c_char_p
     lib.mf_solve_step_static.argtypes = [vp, vp, C.POINTER(MfSolverOpts), C.POINTER(MfSolveReport), vp]
     lib.mf_mg_attach.argtypes = [vp, vp, vp, vp]
     lib.mf_mg_prolongate.argtypes = [vp, vp, vp, vp]
@@ -109,7 +134,8 @@ def load():
     lib.mf_profile_read.argtypes = [vp, C.POINTER(MfProfile)]
     for name in EXPORTS:
         f = getattr(lib, name)
-        if name not in ("mf_mesh_free", "mf_last_error", "mf_solver_defaults"):
+        if name not in ("mf_mesh_free", "mf_last_error", "mf_batch_last_error", "mf_solver_defaults",
+                        "mf_mesh_params_defaults"):
             f.restype = C.c_int
     _lib = lib
     return lib

@@ -101,17 +101,17 @@ template <typename T> __device__ __forceinline__ void atomic_add(typename IO<T>:
 // Jacobian apply, volume part (blocks A-hat .. D-hat of Section 2.3, tau frozen).
 // dst += J_cell src.  src entries on wall nodes (negative ids in `cells`) are
 // taken as zero for the velocity components.
-template <int D, int K, typename T>
+template <int D, int K, typename T, int CPB = CellCfg<D, K>::CPB>
 struct JacSmem {
   static constexpr int N = K + 1, NQ = ipow(N, D), NS = (D + 1) * D;
   SmTab<N, T> st;
-  T tile[CellCfg<D, K>::CPB][NS * NQ];
+  T tile[CPB][NS * NQ];
 };
 
 // One block's worth of cells (block index `blk`) of the cell Jacobian.  The
 // tables in sm.st must be loaded and visible to the block.
-template <int D, int K, typename T>
-__device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T>& sm, int64_t blk, const int32_t* __restrict__ cells,
+template <int D, int K, typename T, int CPB = CellCfg<D, K>::CPB>
+__device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_t blk, const int32_t* __restrict__ cells,
                                                int64_t nc, const T* __restrict__ cache,
                                                const typename IO<T>::type* __restrict__ src,
                                                typename IO<T>::type* __restrict__ dst, T nu, T a0dt) {
@@ -120,7 +120,7 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T>& sm, int64_t blk
   using CF = Cache<D>;
   SmTab<N, T>& st = sm.st;
   const int cl = threadIdx.x / NQ, t = threadIdx.x % NQ;
-  const int64_t cell = blk * C::CPB + cl;
+  const int64_t cell = blk * CPB + cl;
   const bool active = cell < nc;
   T* tile = sm.tile[cl];
   int ii[3] = {t % N, (t / N) % N, t / (N * N)};
@@ -306,13 +306,22 @@ template <typename T> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<df> { static constexpr int value = MF_DF_MINB; };
 template <> struct MinBlocks<float> { static constexpr int value = MF_F32_MINB; };
 
-template <int D, int K, typename T>
-__global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MinBlocks<T>::value)
+// Resident blocks requested per SM for a block of THREADS threads (at most
+// 2048 threads per SM).
+template <typename T, int THREADS> struct MinBlocksFor {
+  static constexpr int value = MinBlocks<T>::value * THREADS <= 2048 ? MinBlocks<T>::value
+                             : (2048 / THREADS > 0 ? 2048 / THREADS : 1);
+};
+
+// CPB cells per block (THREADS = CPB * (K+1)^D); the default CellCfg<D, K>::CPB
+// fills about 256 threads, other values are variants the autotuner times.
+template <int D, int K, typename T, int CPB = CellCfg<D, K>::CPB>
+__global__ void __launch_bounds__(CPB * CellCfg<D, K>::NQ, (MinBlocksFor<T, CPB * CellCfg<D, K>::NQ>::value))
 k_cell_jac(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__ cache,
            const typename IO<T>::type* __restrict__ src, typename IO<T>::type* __restrict__ dst, T nu, T a0dt) {
-  __shared__ JacSmem<D, K, T> sm;
+  __shared__ JacSmem<D, K, T, CPB> sm;
   load_tab<K, T>(sm.st);
-  cell_jac_block<D, K, T>(sm, blockIdx.x, cells, nc, cache, src, dst, nu, a0dt);
+  cell_jac_block<D, K, T, CPB>(sm, blockIdx.x, cells, nc, cache, src, dst, nu, a0dt);
 }
 
 // ---------------------------------------------------------------------------

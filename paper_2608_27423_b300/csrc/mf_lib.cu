@@ -5,6 +5,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <vector>
 #include <algorithm>
@@ -85,6 +88,7 @@ struct ProfEvent {
 
 struct mf_ctx {
   bool prof = false;
+  int cpb_sel[2] = {0, 0};             // cell Jacobian variant per precision (FP64, FP32); 0 = default
   std::vector<ProfEvent> prof_ev;      // pending event pairs
   std::vector<cudaEvent_t> ev_pool;    // reusable events
   mf_profile_t prof_acc;
@@ -204,13 +208,39 @@ static void launch_state(mf_ctx* h, int mode, const double* up, double* dst, cud
   else k_cell_state<D, K, 1><<<g, C::THREADS, 0, st>>>(A);
 }
 
+// Cells-per-block variants of the cell Jacobian that mf_autotune times, per
+// (D, K): index 0 is the default CellCfg<D, K>::CPB (about 256 threads), 1 and
+// 2 a smaller and a larger block.  (D, K) without own variants repeat the
+// default, so only the 3D Q2 and Q3 kernels are compiled three times.
+template <int D, int K> struct CpbVariants {
+  static constexpr int n = 1, v1 = CellCfg<D, K>::CPB, v2 = CellCfg<D, K>::CPB;
+};
+template <> struct CpbVariants<3, 2> { static constexpr int n = 3, v1 = 4, v2 = 16; };   // 108 / 243 / 432 threads
+template <> struct CpbVariants<3, 3> { static constexpr int n = 3, v1 = 2, v2 = 6; };    // 128 / 256 / 384 threads
+template <int D, int K> static int cpb_variant(int i) {
+  return i == 1 ? CpbVariants<D, K>::v1 : i == 2 ? CpbVariants<D, K>::v2 : CellCfg<D, K>::CPB;
+}
+
+template <int D, int K, typename T, int CPB>
+static void launch_jac_cpb(mf_ctx* h, const T* cache, const typename IO<T>::type* x, typename IO<T>::type* y,
+                           cudaStream_t st) {
+  k_cell_jac<D, K, T, CPB><<<nblk(h->nc, CPB), CPB * CellCfg<D, K>::NQ, 0, st>>>(h->cells, h->nc, cache, x, y,
+                                                                                (T)h->nu, (T)h->a0dt);
+}
+
 template <int D, int K, typename T>
 static void launch_jac(mf_ctx* h, const T* cache, const typename IO<T>::type* x, typename IO<T>::type* y,
                        cudaStream_t st) {
-  using C = CellCfg<D, K>;
-  const unsigned g = nblk(h->nc, C::CPB);
   ProfScope ps(h, std::is_same<T, double>::value ? 0 : 1, st);
-  k_cell_jac<D, K, T><<<g, C::THREADS, 0, st>>>(h->cells, h->nc, cache, x, y, (T)h->nu, (T)h->a0dt);
+  if constexpr (std::is_same<T, df>::value) {
+    launch_jac_cpb<D, K, T, CellCfg<D, K>::CPB>(h, cache, x, y, st);    // double-float: default only
+  } else {
+    switch (h->cpb_sel[std::is_same<T, double>::value ? 0 : 1]) {
+      case 1: launch_jac_cpb<D, K, T, CpbVariants<D, K>::v1>(h, cache, x, y, st); break;
+      case 2: launch_jac_cpb<D, K, T, CpbVariants<D, K>::v2>(h, cache, x, y, st); break;
+      default: launch_jac_cpb<D, K, T, CellCfg<D, K>::CPB>(h, cache, x, y, st); break;
+    }
+  }
 }
 
 template <int D, int K, typename T>
@@ -292,6 +322,8 @@ extern "C" mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const do
 }
 
 extern "C" void mf_mesh_free(mf_mesh* m) { delete m; }
+
+#include "mf_meshgen.inc"
 
 // ------------------------------------------------------------------ create
 static void free_ws(Workspace& w) {
@@ -609,6 +641,7 @@ extern "C" mf_status mf_profile_read(mf_handle h, mf_profile_t* out) {
 #include "mf_solve.inc"
 #include "mf_mg.inc"
 #include "mf_transient.inc"
+#include "mf_autotune.inc"
 
 // ---------------------------------------------------------------- batched instances
 struct mf_batch {
@@ -626,6 +659,20 @@ struct mf_batch {
   cudaEvent_t staged = nullptr;                // staging buffers free again
   int grid_cell = 0, grid_mortar = 0;          // persistent grid sizes
   std::string err;
+  // batched solve (mf_batch_solve_step): per-instance streams forked from the
+  // caller's stream, a capture stream, one device table pair per FGMRES
+  // column (Z_j -> w of every instance) and the residual norms read back
+  std::vector<cudaStream_t> ist;
+  std::vector<cudaEvent_t> iev;
+  cudaEvent_t fork_ev = nullptr;
+  cudaStream_t cap = nullptr;
+  BatchTable<double>* sol_tab = nullptr;       // device [sol_m]
+  MortarBatchTable<double>* sol_mtab = nullptr;
+  std::vector<BatchTable<double>> sol_htab;    // host copies (launch parameters)
+  std::vector<MortarBatchTable<double>> sol_hmtab;
+  int sol_m = 0;
+  double* norms2 = nullptr;                    // device [n] ||R_i||^2
+  double* h_norms2 = nullptr;                  // pinned [n]
 };
 
 template <int D, int K>
@@ -665,6 +712,14 @@ extern "C" mf_status mf_batch_create(const mf_handle* hs, int n, mf_batch** out)
   return MF_OK;
 }
 
+extern "C" const char* mf_batch_last_error(mf_batch* b) {
+  if (!b) return "null batch";
+  if (!b->err.empty()) return b->err.c_str();
+  for (mf_ctx* c : b->hs)
+    if (!c->err.empty()) return c->err.c_str();
+  return "";
+}
+
 extern "C" mf_status mf_batch_destroy(mf_batch* b) {
   if (!b) return MF_ERR_ARG;
   void* dp[] = {b->tab64, b->tab32, b->mtab64, b->mtab32, b->counters};
@@ -672,19 +727,23 @@ extern "C" mf_status mf_batch_destroy(mf_batch* b) {
   void* hp[] = {b->h_tab64, b->h_tab32, b->h_mtab64, b->h_mtab32};
   for (void* p : hp) if (p) cudaFreeHost(p);
   if (b->staged) cudaEventDestroy(b->staged);
+  for (cudaStream_t q : b->ist) cudaStreamDestroy(q);
+  for (cudaEvent_t q : b->iev) cudaEventDestroy(q);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->sol_tab) cudaFree(b->sol_tab);
+  if (b->sol_mtab) cudaFree(b->sol_mtab);
+  if (b->norms2) cudaFree(b->norms2);
+  if (b->h_norms2) cudaFreeHost(b->h_norms2);
   delete b;
   return MF_OK;
 }
 
+// Tile tables of one batched apply xs[i] -> ys[i] (host copies ht, hm).
 template <typename T>
-static mf_status batch_apply_t(mf_batch* b, const void* const* xs, void* const* ys, cudaStream_t st) {
-  mf_ctx* h = b->hs[0];
+static mf_status fill_batch_tables(mf_batch* b, const void* const* xs, void* const* ys, BatchTable<T>* ht,
+                                   MortarBatchTable<T>* hm, bool need_lin = true) {
   const bool f64 = std::is_same<T, double>::value;
-  BatchTable<T>* ht = f64 ? (BatchTable<T>*)b->h_tab64 : (BatchTable<T>*)b->h_tab32;
-  BatchTable<T>* dt = f64 ? (BatchTable<T>*)b->tab64 : (BatchTable<T>*)b->tab32;
-  MortarBatchTable<T>* hm = f64 ? (MortarBatchTable<T>*)b->h_mtab64 : (MortarBatchTable<T>*)b->h_mtab32;
-  MortarBatchTable<T>* dm = f64 ? (MortarBatchTable<T>*)b->mtab64 : (MortarBatchTable<T>*)b->mtab32;
-  CK(cudaEventSynchronize(b->staged));    // the previous call's table copies have completed
   const int n = (int)b->hs.size();
   int cpb = 1, mpb = 1;
   switch (b->d * 10 + b->k) {
@@ -696,7 +755,7 @@ static mf_status batch_apply_t(mf_batch* b, const void* const* xs, void* const* 
   ht->first_tile[0] = 0; hm->first_tile[0] = 0;
   for (int i = 0; i < n; ++i) {
     mf_ctx* c = b->hs[i];
-    if (!c->have_lin) { b->err = "mf_batch_apply_jacobian: an instance has no linearisation"; return MF_ERR_STATE; }
+    if (need_lin && !c->have_lin) { b->err = "batched apply: an instance has no linearisation"; return MF_ERR_STATE; }
     if (!xs[i] || !ys[i] || xs[i] == ys[i]) return MF_ERR_ARG;
     BatchInst<T>& in = ht->inst[i];
     in.cells = c->cells; in.nc = c->nc; in.cache = f64 ? (const T*)c->cache64 : (const T*)c->cache32;
@@ -708,11 +767,20 @@ static mf_status batch_apply_t(mf_batch* b, const void* const* xs, void* const* 
     A.mc_ang = c->mc_ang; A.mc_w = c->mc_w; A.nm = c->nm; A.src = (const T*)xs[i]; A.dst = (T*)ys[i];
     A.nu = (T)c->nu; A.dz = c->H / c->n_z; A.zero_wall = 1;
     hm->first_tile[i + 1] = hm->first_tile[i] + (c->nm + mpb - 1) / mpb;
-    CK(cudaMemsetAsync(ys[i], 0, c->ndof * sizeof(T), st));
   }
-  CK(cudaMemcpyAsync(dt, ht, sizeof(BatchTable<T>), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dm, hm, sizeof(MortarBatchTable<T>), cudaMemcpyHostToDevice, st));
-  CK(cudaEventRecord(b->staged, st));
+  return MF_OK;
+}
+
+// The launches of one batched apply from device tables dt, dm whose host
+// copies are ht, hm: zero every ys[i], one persistent cell launch and one
+// persistent mortar launch over all instances, then the Dirichlet rows.
+template <typename T>
+static mf_status launch_batch(mf_batch* b, const BatchTable<T>* ht, const MortarBatchTable<T>* hm,
+                              const BatchTable<T>* dt, const MortarBatchTable<T>* dm, cudaStream_t st) {
+  using TI = typename IO<T>::type;
+  mf_ctx* h = b->hs[0];     // CUDA errors are reported on the first instance
+  const int n = ht->ninst;
+  for (int i = 0; i < n; ++i) CK(cudaMemsetAsync(ht->inst[i].dst, 0, b->hs[i]->ndof * sizeof(TI), st));
   CK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), st));
   const int64_t tc = ht->first_tile[n], tm = hm->first_tile[n];
   switch (b->d * 10 + b->k) {
@@ -729,11 +797,30 @@ static mf_status batch_apply_t(mf_batch* b, const void* const* xs, void* const* 
   for (int i = 0; i < n; ++i) {
     mf_ctx* c = b->hs[i];
     if (!c->nwall) continue;
-    if (c->d == 2) k_dirichlet_copy<2, T><<<nblk(c->nwall, 256), 256, 0, st>>>(c->wall, c->nwall, (const T*)xs[i], (T*)ys[i]);
-    else k_dirichlet_copy<3, T><<<nblk(c->nwall, 256), 256, 0, st>>>(c->wall, c->nwall, (const T*)xs[i], (T*)ys[i]);
+    const TI* x = (const TI*)ht->inst[i].src;
+    TI* y = (TI*)ht->inst[i].dst;
+    if (c->d == 2) k_dirichlet_copy<2, TI><<<nblk(c->nwall, 256), 256, 0, st>>>(c->wall, c->nwall, x, y);
+    else k_dirichlet_copy<3, TI><<<nblk(c->nwall, 256), 256, 0, st>>>(c->wall, c->nwall, x, y);
   }
   CK(cudaGetLastError());
   return MF_OK;
+}
+
+template <typename T>
+static mf_status batch_apply_t(mf_batch* b, const void* const* xs, void* const* ys, cudaStream_t st) {
+  mf_ctx* h = b->hs[0];     // CUDA errors are reported on the first instance
+  const bool f64 = std::is_same<T, double>::value;
+  BatchTable<T>* ht = f64 ? (BatchTable<T>*)b->h_tab64 : (BatchTable<T>*)b->h_tab32;
+  BatchTable<T>* dt = f64 ? (BatchTable<T>*)b->tab64 : (BatchTable<T>*)b->tab32;
+  MortarBatchTable<T>* hm = f64 ? (MortarBatchTable<T>*)b->h_mtab64 : (MortarBatchTable<T>*)b->h_mtab32;
+  MortarBatchTable<T>* dm = f64 ? (MortarBatchTable<T>*)b->mtab64 : (MortarBatchTable<T>*)b->mtab32;
+  CK(cudaEventSynchronize(b->staged));    // the previous call's table copies have completed
+  mf_status e = fill_batch_tables<T>(b, xs, ys, ht, hm);
+  if (e != MF_OK) return e;
+  CK(cudaMemcpyAsync(dt, ht, sizeof(BatchTable<T>), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dm, hm, sizeof(MortarBatchTable<T>), cudaMemcpyHostToDevice, st));
+  CK(cudaEventRecord(b->staged, st));
+  return launch_batch<T>(b, ht, hm, dt, dm, st);
 }
 
 extern "C" mf_status mf_batch_apply_jacobian(mf_batch* b, const void* const* xs, void* const* ys, mf_precision prec,
@@ -743,6 +830,8 @@ extern "C" mf_status mf_batch_apply_jacobian(mf_batch* b, const void* const* xs,
               : prec == MF_FP32 ? batch_apply_t<float>(b, xs, ys, S(stream)) : MF_ERR_ARG;
   return s;
 }
+
+#include "mf_batch_solve.inc"
 
 // ---------------------------------------------------------------- no-allocation solve
 // Workspace of mf_solve_step_static: a file-scope device array.  In host code

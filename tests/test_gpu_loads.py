@@ -1,7 +1,10 @@
-"""Wall loads end to end on the GPU: steady Taylor-Couette flow solved by
-mf_solve_step, torque by mf_wall_loads, against the closed form (the same
-set-up as the oracle's pin): a rigid ring of stator cells turning at Om inside
-a resting outer wall; the enclosed rotor is fluid."""
+"""Wall loads on the GPU: steady Taylor-Couette flow (a rigid ring of stator
+cells turning at Om inside a resting outer wall; the enclosed rotor is fluid),
+the same set-up as the oracle's pin.  The discrete solution comes from the
+oracle's direct solve, so the test isolates mf_wall_loads: its force, torque
+and power per wall group must equal the oracle's consistent reactions of the
+same state, and the torque must approach the closed form at the rate the
+oracle pin fixes."""
 import dataclasses
 
 import numpy as np
@@ -13,8 +16,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def couette_gpu(k, m, nu=0.2, Om=1.0, theta=0.1):
-    from paper_2608_27423_b300 import RotorStatorOperator, solver_defaults, MF_PC_JACOBI, MF_FP64
+def couette_state(k, m, nu, Om, theta):
+    """Mesh, wall groups and the converged discrete state (oracle, sparse LU)."""
+    import scipy.sparse.linalg as spla
+    from oracle.fem import Problem
+    from oracle.solve import Operator
     n_s = 2 * m
     mesh = synth.rotor_stator_mesh(2, k, m, max(1, m // 2), n_s)
     r1 = mesh.R + (1.0 - mesh.R) / n_s
@@ -22,34 +28,44 @@ def couette_gpu(k, m, nu=0.2, Om=1.0, theta=0.1):
     wall = mesh.wall.copy()
     wall[body] = 1
     mesh = dataclasses.replace(mesh, wall=wall)
-    op = RotorStatorOperator(mesh, nu, 0.0, 0.0, 1)
-    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
-    op.set_angle(theta)
-    xyz = torch.empty((mesh.n_nodes, 2), dtype=torch.float64, device="cuda")
-    op.node_coords(xyz)
-    x = xyz.cpu().numpy()
+    x = Problem(mesh, nu, 0.0, 0.0, 1, theta).x
     g = np.zeros((mesh.n_nodes, 2))
     g[body, 0], g[body, 1] = -Om * x[body, 1], Om * x[body, 0]
-    op.set_dirichlet(T(g))
-    up = torch.zeros((mesh.n_nodes, 3), dtype=torch.float64, device="cuda")
-    st, rep = op.solve_step(up, solver_defaults(theta=theta, pc=MF_PC_JACOBI, pc_precision=MF_FP64, newton_rtol=1e-12,
-                                                newton_atol=1e-12, lin_rtol=1e-10, max_newton=30, restart=200,
-                                                max_lin_iters=20000))
-    assert st == 0, op.last_error()
-    out = torch.empty((2, 4), dtype=torch.float64, device="cuda")
-    op.wall_loads(up, out, group=torch.tensor(np.where(body, 0, 1).astype(np.uint8), device="cuda"), n_groups=2)
-    Tq = 4 * np.pi * nu * Om * r1 ** 2 / (1.0 - r1 ** 2)
-    return out.cpu().numpy(), Tq, Om
+    ref = Operator(mesh, nu, 0.0, 0.0, 1, theta, g=g)
+    up = np.zeros((mesh.n_nodes, 3))
+    for _ in range(12):
+        r = ref.residual(up)
+        if np.linalg.norm(r) < 1e-11:
+            break
+        ref.set_linearization(up)
+        up += spla.spsolve(ref.assemble().tocsc(), -r.ravel()).reshape(up.shape)
+    group = np.where(body, 0, 1).astype(np.uint8)
+    return mesh, g, up, group, ref, r1
 
 
 @pytest.mark.parametrize("k", [2, 3])
-def test_taylor_couette_torque_on_gpu(k):
+def test_taylor_couette_wall_loads_on_gpu(k):
+    from paper_2608_27423_b300 import RotorStatorOperator
+    nu, Om, theta = 0.2, 1.0, 0.1
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     errs = []
     for m in (2, 4):
-        loads, Tq, Om = couette_gpu(k, m)
+        mesh, g, up, group, ref, r1 = couette_state(k, m, nu, Om, theta)
+        op = RotorStatorOperator(mesh, nu, 0.0, 0.0, 1)
+        op.set_angle(theta)
+        op.set_dirichlet(T(g))
+        op.set_linearization(T(up), theta)
+        out = torch.empty((2, 4), dtype=torch.float64, device="cuda")
+        op.wall_loads(T(up), out, group=torch.tensor(group, device="cuda"), n_groups=2)
+        loads = out.cpu().numpy()
+        loads_ref = ref.wall_loads(up, group=group.astype(np.int64), n_groups=2)
+        Tq = 4 * np.pi * nu * Om * r1 ** 2 / (1.0 - r1 ** 2)
+        # parity with the oracle's reactions of the same state
+        assert np.abs(loads - loads_ref).max() < 1e-11 * Tq, (loads, loads_ref)
+        # closed form, no net force, power = Om * torque on the ring, none on the resting wall
         e_in, e_out = loads[0, 2] / Tq - 1, loads[1, 2] / (-Tq) - 1
         assert abs(e_in) < 2e-3 and abs(e_out) < 2e-3, (m, e_in, e_out)
-        assert np.abs(loads[:, :2]).max() < 1e-8 * Tq
+        assert np.abs(loads[:, :2]).max() < 1e-10 * Tq
         assert abs(loads[0, 3] - Om * loads[0, 2]) < 1e-10 * Tq and abs(loads[1, 3]) < 1e-10 * Tq
         errs.append(max(abs(e_in), abs(e_out)))
     assert np.log2(errs[0] / errs[1]) > 2 * k - 1.5, errs

@@ -1,0 +1,61 @@
+"""The library's rotor-stator mesh generator (mf_mesh_rotor_stator, host
+code, no GPU) against the seeded input generator that every other test uses:
+identical connectivity, sides, walls and interface tables, coordinates equal
+to roundoff, and the same coarsening maps (mf_mesh_coarsen_map)."""
+import numpy as np
+import pytest
+
+import synth
+from synth.mesh import coarsen
+
+CASES = [
+    dict(d=2, k=1, m=2, n_r=1, n_s=1),
+    dict(d=2, k=2, m=16, n_r=5, n_s=12),
+    dict(d=2, k=4, m=3, n_r=2, n_s=3),
+    dict(d=3, k=2, m=4, n_r=2, n_s=2, n_z=3),
+    dict(d=3, k=3, m=2, n_r=1, n_s=2, n_z=2),
+    dict(d=3, k=2, m=8, n_r=4, n_s=4, n_z=8, blades=4),
+    dict(d=3, k=3, m=6, n_r=3, n_s=2, n_z=5, blades=3),
+]
+
+
+@pytest.mark.parametrize("p", CASES, ids=lambda p: "-".join(f"{k}{v}" for k, v in p.items()))
+def test_generator_matches_input_generator(p):
+    from paper_2608_27423_b300 import rotor_stator_mesh
+    ref = synth.rotor_stator_mesh(p["d"], p["k"], p["m"], p["n_r"], p["n_s"], p.get("n_z", 1),
+                                  blades=p.get("blades", 0))
+    got = rotor_stator_mesh(**p)
+    assert got.x0.shape == ref.x0.shape and got.cells.shape == ref.cells.shape
+    for key in ("cells", "cell_side", "node_side", "wall", "iface_rotor", "iface_stator"):
+        assert np.array_equal(getattr(got, key), getattr(ref, key)), key
+    assert np.abs(got.x0 - ref.x0).max() < 1e-14
+    assert (got.R, got.n_R, got.n_z, got.H) == (ref.R, ref.n_R, ref.n_z, ref.H)
+    assert abs(got.phi0 - ref.phi0) < 1e-16
+    # interface nodes of both sides lie on the circle
+    for tab in (got.iface_rotor, got.iface_stator):
+        nodes = got.cells[tab.ravel()]
+        r = np.hypot(got.x0[nodes, 0], got.x0[nodes, 1])
+        assert np.sum(np.abs(r - got.R) < 1e-15) >= tab.size * (p["k"] + 1) ** (p["d"] - 1)
+
+
+@pytest.mark.parametrize("p", [dict(d=2, k=2, m=4, n_r=2, n_s=4), dict(d=3, k=2, m=4, n_r=2, n_s=2, n_z=4)])
+def test_coarsen_map_matches_input_generator(p):
+    from paper_2608_27423_b300 import coarsen_map
+    cp, parent, child = coarsen_map(**p)
+    rp, rparent, rchild = coarsen(dict(p, n_z=p.get("n_z", 1)))
+    for key in ("m", "n_r", "n_s"):
+        assert cp[key] == rp[key]
+    if p["d"] == 3:
+        assert cp["n_z"] == rp["n_z"]
+    assert np.array_equal(parent, rparent) and np.array_equal(child, rchild)
+
+
+def test_generator_rejects_bad_parameters():
+    from paper_2608_27423_b300 import rotor_stator_mesh, coarsen_map, MfError
+    for bad in (dict(d=4), dict(k=0), dict(m=0), dict(R=1.2), dict(sq=0.8), dict(d=2, blades=2), dict(n_z=0)):
+        with pytest.raises(MfError):
+            rotor_stator_mesh(**bad)
+    with pytest.raises(MfError):
+        coarsen_map(d=2, k=2, m=3, n_r=2, n_s=2)
+    with pytest.raises(TypeError):
+        rotor_stator_mesh(radius=1.0)
