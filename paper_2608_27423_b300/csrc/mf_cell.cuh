@@ -10,6 +10,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 #include "mf_tables.h"
 #include "mf_df64.cuh"
 
@@ -101,12 +102,34 @@ template <typename T> __device__ __forceinline__ void atomic_add(typename IO<T>:
 // Jacobian apply, volume part (blocks A-hat .. D-hat of Section 2.3, tau frozen).
 // dst += J_cell src.  src entries on wall nodes (negative ids in `cells`) are
 // taken as zero for the velocity components.
+// FP32 applies stage the block's slice of the per-point cache in shared
+// memory with asynchronous copies issued at kernel entry, so the loads overlap
+// the gather and the sum-factorisation sweeps instead of stalling the point
+// physics (the FP32 kernel is latency-bound on them; the FP64 kernel is bound
+// by the FP64 pipe and keeps direct loads).  On when the block's shared
+// memory stays within the 48 KB static limit.
+template <int D, int K, typename T, int CPB> struct StageCfg {
+  static constexpr int NQ = ipow(K + 1, D), NS = (D + 1) * D, THREADS = CPB * NQ;
+  static constexpr size_t bytes = sizeof(T) * ((size_t)THREADS * Cache<D>::NF + (size_t)CPB * NS * NQ + 5 * (K + 1) * (K + 1));
+  static constexpr bool on = std::is_same<T, float>::value && bytes <= 48 * 1024;
+};
+
 template <int D, int K, typename T, int CPB = CellCfg<D, K>::CPB>
 struct JacSmem {
   static constexpr int N = K + 1, NQ = ipow(N, D), NS = (D + 1) * D;
   SmTab<N, T> st;
   T tile[CPB][NS * NQ];
+  T stage[StageCfg<D, K, T, CPB>::on ? Cache<D>::NF * CPB * NQ : 1];
 };
+
+// 4-byte asynchronous global -> shared copy (completes at cp_async_wait_all,
+// visible to the issuing thread).
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // One block's worth of cells (block index `blk`) of the cell Jacobian.  The
 // tables in sm.st must be loaded and visible to the block.
@@ -125,6 +148,22 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_
   T* tile = sm.tile[cl];
   int ii[3] = {t % N, (t / N) % N, t / (N * N)};
   const int strd[3] = {1, N, N * N};
+  constexpr bool STAGE = StageCfg<D, K, T, CPB>::on;
+  constexpr int THREADS = CPB * NQ;
+  if constexpr (STAGE) {
+    // this point's cache entries -> stage[f][threadIdx.x]; a point past the
+    // last cell stages zeros (its results are never scattered)
+    if (active) {
+      const int64_t P = nc * NQ;
+      const T* cp = cache + cell * NQ + t;
+#pragma unroll
+      for (int f = 0; f < CF::NF; ++f) cp_async4(&sm.stage[f * THREADS + threadIdx.x], cp + f * P);
+    } else {
+#pragma unroll
+      for (int f = 0; f < CF::NF; ++f) sm.stage[f * THREADS + threadIdx.x] = T(0);
+    }
+    cp_async_commit();
+  }
 
   T v[NF];
   int node = 0;
@@ -196,25 +235,31 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_
   {
     const int64_t P = nc * NQ;
     const T* cp = cache + (active ? cell * NQ + t : 0);
+    if constexpr (STAGE) cp_async_wait_all();
+    // cache entry f of this point: staged copy or direct load
+    auto ld = [&](int f) -> T {
+      if constexpr (STAGE) return sm.stage[f * THREADS + threadIdx.x];
+      else return cp[f * P];
+    };
     T Ji[D][D], a[D], gU[D][D], Rs[D], G[Sym<D>::n], ct[D];
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
-      for (int m = 0; m < D; ++m) Ji[r][m] = cp[(CF::JINV + r * D + m) * P];
-    const T Wq = cp[CF::W * P];
+      for (int m = 0; m < D; ++m) Ji[r][m] = ld(CF::JINV + r * D + m);
+    const T Wq = ld(CF::W);
 #pragma unroll
-    for (int e = 0; e < Sym<D>::n; ++e) G[e] = cp[(CF::G + e) * P];
+    for (int e = 0; e < Sym<D>::n; ++e) G[e] = ld(CF::G + e);
 #pragma unroll
-    for (int r = 0; r < D; ++r) ct[r] = cp[(CF::CT + r) * P];
+    for (int r = 0; r < D; ++r) ct[r] = ld(CF::CT + r);
 #pragma unroll
-    for (int m = 0; m < D; ++m) a[m] = cp[(CF::A + m) * P];
+    for (int m = 0; m < D; ++m) a[m] = ld(CF::A + m);
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
-      for (int m = 0; m < D; ++m) gU[c][m] = cp[(CF::GU + c * D + m) * P];
+      for (int m = 0; m < D; ++m) gU[c][m] = ld(CF::GU + c * D + m);
 #pragma unroll
-    for (int c = 0; c < D; ++c) Rs[c] = cp[(CF::RS + c) * P];
-    const T tau = cp[CF::TAU * P];
+    for (int c = 0; c < D; ++c) Rs[c] = ld(CF::RS + c);
+    const T tau = ld(CF::TAU);
 
     T gw[D][D], gr[D], lap[D], gal[D], Rl[D];
 #pragma unroll
@@ -306,17 +351,25 @@ template <typename T> struct MinBlocks { static constexpr int value = 1; };
 template <> struct MinBlocks<df> { static constexpr int value = MF_DF_MINB; };
 template <> struct MinBlocks<float> { static constexpr int value = MF_F32_MINB; };
 
-// Resident blocks requested per SM for a block of THREADS threads (at most
-// 2048 threads per SM).
-template <typename T, int THREADS> struct MinBlocksFor {
-  static constexpr int value = MinBlocks<T>::value * THREADS <= 2048 ? MinBlocks<T>::value
-                             : (2048 / THREADS > 0 ? 2048 / THREADS : 1);
+// Launch shape of the cell Jacobian with CPB cells per block: resident blocks
+// requested per SM = MinBlocks<T>, lowered so that the blocks fit the SM's
+// 2048 threads and 228 KB of shared memory and keep at least 48 registers per
+// thread (fewer spill).
+template <int D, int K, typename T, int CPB> struct JacLaunch {
+  static constexpr int THREADS = CPB * CellCfg<D, K>::NQ;
+  static constexpr int by_threads = 2048 / THREADS;
+  static constexpr int by_smem = (int)(233472 / (sizeof(JacSmem<D, K, T, CPB>) + 1024));
+  static constexpr int by_regs = 65536 / (THREADS * 48);
+  static constexpr int m0 = MinBlocks<T>::value < by_threads ? MinBlocks<T>::value : by_threads;
+  static constexpr int m1 = m0 < by_smem ? m0 : by_smem;
+  static constexpr int m2 = m1 < by_regs ? m1 : by_regs;
+  static constexpr int MINB = m2 > 1 ? m2 : 1;
 };
 
 // CPB cells per block (THREADS = CPB * (K+1)^D); the default CellCfg<D, K>::CPB
 // fills about 256 threads, other values are variants the autotuner times.
 template <int D, int K, typename T, int CPB = CellCfg<D, K>::CPB>
-__global__ void __launch_bounds__(CPB * CellCfg<D, K>::NQ, (MinBlocksFor<T, CPB * CellCfg<D, K>::NQ>::value))
+__global__ void __launch_bounds__(JacLaunch<D, K, T, CPB>::THREADS, JacLaunch<D, K, T, CPB>::MINB)
 k_cell_jac(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__ cache,
            const typename IO<T>::type* __restrict__ src, typename IO<T>::type* __restrict__ dst, T nu, T a0dt) {
   __shared__ JacSmem<D, K, T, CPB> sm;

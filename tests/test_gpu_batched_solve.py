@@ -68,7 +68,7 @@ def _run(cases, batched, use_graph):
         ops.append(g)
         ups.append(T(u0))
     batch = BatchedOperators(ops)
-    o = solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=20, newton_rtol=1e-10, max_newton=40)
+    o = solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=20, newton_rtol=1e-12, max_newton=40)
     st, reps = batch.solve_step(ups, [c[1]["theta"] for c in cases], o, krylov_iters=10, batched=batched,
                                 use_graph=use_graph)
     torch.cuda.synchronize()
@@ -83,9 +83,10 @@ def test_batched_solve_reaches_oracle_solutions(cases):
         assert 1 <= it <= 40 and rep.status == 0
         r0 = np.linalg.norm(op.residual(u0))
         assert abs(rep.res_norm[0] - r0) <= 1e-12 * r0
-        # the reported final norm is the oracle's residual norm of the returned state
+        # the reported final norm is the oracle's residual norm of the returned
+        # state, up to the rounding of the two residual evaluations (~1e-13 R_0)
         rf = np.linalg.norm(op.residual(up))
-        assert rf <= 1.01e-10 * r0 and abs(rep.res_norm[it] - rf) <= 1e-3 * rf + 1e-14 * r0
+        assert rf <= 1e-12 * r0 + 1e-13 * r0 and abs(rep.res_norm[it] - rf) <= 1e-3 * rf + 1e-13 * r0
         du, dp = _rel(up, ref)
         assert du < 1e-8 and dp < 1e-6, (du, dp)
 
