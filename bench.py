@@ -391,6 +391,33 @@ def cpu_oracle_rate(mesh, prm, f, seconds):
     return rate, sample, t_full
 
 
+def cpu_oracle_2d():
+    """The oracle's two evaluation paths on the whole 2D workload (576 + 768 Q2
+    quads): (A) element matrices assembled to CSR, then SpMV; (B) the
+    matrix-free per-point apply.  Returns DoFs/s of each (median of 5, B of 3)
+    and the assembly time."""
+    from oracle.solve import Operator
+    mesh, prm, f = synth.make_config("2d_q2")
+    op = Operator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"], prm["theta"], up_star=f["up_star"],
+                  u_n=f["u_n"], u_nm1=f["u_nm1"])
+    tb = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        op.apply(f["x"])
+        tb.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    A = op.assemble().tocsr()
+    t_asm = time.perf_counter() - t0
+    xv = f["x"].ravel()
+    ta = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        A @ xv
+        ta.append(time.perf_counter() - t0)
+    return {"workload": "2d_q2", "n_dofs": mesh.n_dofs, "path_A_csr_spmv_dofs_per_s": mesh.n_dofs / np.median(ta),
+            "path_A_assembly_s": t_asm, "path_B_matrix_free_dofs_per_s": mesh.n_dofs / np.median(tb)}
+
+
 def cpu_cores_used():
     try:
         import threadpoolctl
@@ -543,7 +570,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, sample, t_full = cpu_oracle_rate(mesh, prm, f, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "DoFs/s", "cores": cpu_cores_used(), "kind": "oracle",
-                                "sample": sample}
+                                "sample": sample, "oracle_2d": cpu_oracle_2d()}
     if rank == 0:
         print(json.dumps(line, default=float), flush=True)
     if dist:
