@@ -740,11 +740,14 @@ extern "C" mf_status mf_batch_destroy(mf_batch* b) {
 }
 
 // Tile tables of one batched apply xs[i] -> ys[i] (host copies ht, hm).
+// sel (optional): the instances (indices into b->hs) that form the table, in
+// order; xs/ys are indexed like sel.  NULL: every instance.
 template <typename T>
 static mf_status fill_batch_tables(mf_batch* b, const void* const* xs, void* const* ys, BatchTable<T>* ht,
-                                   MortarBatchTable<T>* hm, bool need_lin = true) {
+                                   MortarBatchTable<T>* hm, bool need_lin = true, const int* sel = nullptr,
+                                   int nsel = 0) {
   const bool f64 = std::is_same<T, double>::value;
-  const int n = (int)b->hs.size();
+  const int n = sel ? nsel : (int)b->hs.size();
   int cpb = 1, mpb = 1;
   switch (b->d * 10 + b->k) {
 #define CASE(D_, K_) case D_ * 10 + K_: cpb = CellCfg<D_, K_>::CPB; mpb = MortarCfg<D_, K_>::MPB; break;
@@ -754,7 +757,7 @@ static mf_status fill_batch_tables(mf_batch* b, const void* const* xs, void* con
   ht->ninst = n; hm->ninst = n;
   ht->first_tile[0] = 0; hm->first_tile[0] = 0;
   for (int i = 0; i < n; ++i) {
-    mf_ctx* c = b->hs[i];
+    mf_ctx* c = b->hs[sel ? sel[i] : i];
     if (need_lin && !c->have_lin) { b->err = "batched apply: an instance has no linearisation"; return MF_ERR_STATE; }
     if (!xs[i] || !ys[i] || xs[i] == ys[i]) return MF_ERR_ARG;
     BatchInst<T>& in = ht->inst[i];
@@ -776,11 +779,12 @@ static mf_status fill_batch_tables(mf_batch* b, const void* const* xs, void* con
 // persistent mortar launch over all instances, then the Dirichlet rows.
 template <typename T>
 static mf_status launch_batch(mf_batch* b, const BatchTable<T>* ht, const MortarBatchTable<T>* hm,
-                              const BatchTable<T>* dt, const MortarBatchTable<T>* dm, cudaStream_t st) {
+                              const BatchTable<T>* dt, const MortarBatchTable<T>* dm, cudaStream_t st,
+                              const int* sel = nullptr) {
   using TI = typename IO<T>::type;
   mf_ctx* h = b->hs[0];     // CUDA errors are reported on the first instance
   const int n = ht->ninst;
-  for (int i = 0; i < n; ++i) CK(cudaMemsetAsync(ht->inst[i].dst, 0, b->hs[i]->ndof * sizeof(TI), st));
+  for (int i = 0; i < n; ++i) CK(cudaMemsetAsync(ht->inst[i].dst, 0, b->hs[sel ? sel[i] : i]->ndof * sizeof(TI), st));
   CK(cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), st));
   const int64_t tc = ht->first_tile[n], tm = hm->first_tile[n];
   switch (b->d * 10 + b->k) {
@@ -795,7 +799,7 @@ static mf_status launch_batch(mf_batch* b, const BatchTable<T>* ht, const Mortar
 #undef CASE
   }
   for (int i = 0; i < n; ++i) {
-    mf_ctx* c = b->hs[i];
+    mf_ctx* c = b->hs[sel ? sel[i] : i];
     if (!c->nwall) continue;
     const TI* x = (const TI*)ht->inst[i].src;
     TI* y = (TI*)ht->inst[i].dst;
