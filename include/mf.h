@@ -380,13 +380,17 @@ mf_status mf_batch_apply_jacobian(mf_batch* b, const void* const* xs, void* cons
  *   use_graph = 1: one Newton iteration of the whole batch is captured as a
  *                CUDA graph (once per call) and replayed.
  * After each iteration the host reads the n residual norms back (one small
- * copy and a synchronisation) and stops when every instance has ||R_i|| <=
- * newton_rtol ||R_i,0|| or <= newton_atol, or after so->max_newton (<= 64)
- * iterations; every instance takes every iteration.  reps (host, n entries,
- * may be NULL): res_norm[0..newton_iters], lin_iters, wall seconds of the
- * call, status.  Returns MF_OK when every instance converged, otherwise the
- * first failing instance's status (MF_ERR_NOT_CONVERGED or MF_ERR_NAN; ups
- * then hold the last iterates).  Errors: MF_ERR_ARG (null pointers,
+ * copy and a synchronisation).  An instance stops iterating once ||R_i|| <=
+ * newton_rtol ||R_i,0|| or <= newton_atol (the graph and the tile tables are
+ * rebuilt for the remaining ones); the batch stops when none is left or after
+ * so->max_newton (<= 64) iterations.  A step that makes ||R_i|| non-finite or
+ * ten times the smallest ||R_i|| reached so far is halved from the previous
+ * iterate up to so->line_search times until ||R_i|| falls below its previous
+ * value, else the instance keeps its previous iterate and stops.  reps (host, n entries, may be NULL): per instance
+ * res_norm[0..newton_iters], lin_iters, wall seconds of the call, status.
+ * Returns MF_OK when every instance converged, otherwise the first failing
+ * instance's status (MF_ERR_NOT_CONVERGED or MF_ERR_NAN; ups then hold the
+ * last accepted iterates).  Errors: MF_ERR_ARG (null pointers,
  * non-finite angle, pc = MF_PC_CHEBYSHEV, outer_precision != MF_FP64),
  * MF_ERR_STATE (profiling on, MF_PC_MG without levels).  Synchronising.
  * Not part of the paper, which solves one problem at a time. */
