@@ -386,7 +386,8 @@ mf_status mf_batch_apply_jacobian(mf_batch* b, const void* const* xs, void* cons
  * so->max_newton (<= 64) iterations.  A step that makes ||R_i|| non-finite or
  * ten times the smallest ||R_i|| reached so far is halved from the previous
  * iterate up to so->line_search times until ||R_i|| falls below its previous
- * value, else the instance keeps its previous iterate and stops.  reps (host, n entries, may be NULL): per instance
+ * value, else the instance keeps its previous iterate and stops
+ * (line_search = 0: full steps; only a non-finite ||R_i|| stops an instance).  reps (host, n entries, may be NULL): per instance
  * res_norm[0..newton_iters], lin_iters, wall seconds of the call, status.
  * Returns MF_OK when every instance converged, otherwise the first failing
  * instance's status (MF_ERR_NOT_CONVERGED or MF_ERR_NAN; ups then hold the

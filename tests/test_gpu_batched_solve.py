@@ -12,8 +12,8 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# (m, n_r, n_s, Re, theta, seed): 2D Q2 rotor-stator meshes of 80 .. 272 quads
-SPECS = [(4, 2, 3, 10.0, 0.137, 31), (6, 2, 4, 200.0, 0.9, 32), (2, 1, 2, 1.0, 2.3, 33), (4, 1, 4, 50.0, 0.05, 34)]
+# (m, n_r, n_s, Re, theta, seed): 2D Q2 rotor-stator meshes of 28 .. 180 quads
+SPECS = [(4, 2, 3, 10.0, 0.137, 31), (6, 2, 4, 20.0, 0.9, 32), (2, 1, 2, 1.0, 2.3, 33), (4, 1, 4, 50.0, 0.05, 34)]
 
 
 def _instance(m, n_r, n_s, re, theta, seed):
@@ -68,8 +68,10 @@ def _run(cases, batched, use_graph):
         ops.append(g)
         ups.append(T(u0))
     batch = BatchedOperators(ops)
-    o = solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=20, newton_rtol=1e-12, max_newton=40)
-    st, reps = batch.solve_step(ups, [c[1]["theta"] for c in cases], o, krylov_iters=10, batched=batched,
+    # full Newton steps with a strong linear solve: the test is about agreement, not globalisation
+    o = solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=40, newton_rtol=1e-12, max_newton=40,
+                        line_search=0)
+    st, reps = batch.solve_step(ups, [c[1]["theta"] for c in cases], o, krylov_iters=16, batched=batched,
                                 use_graph=use_graph)
     torch.cuda.synchronize()
     return st, reps, [u.cpu().numpy() for u in ups], (batch, ops)
