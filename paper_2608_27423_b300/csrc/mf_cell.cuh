@@ -110,56 +110,15 @@ template <typename T> __device__ __forceinline__ void atomic_add(typename IO<T>:
 // memory stays within the 48 KB static limit.
 template <int D, int K, typename T, int CPB> struct StageCfg {
   static constexpr int NQ = ipow(K + 1, D), NS = (D + 1) * D, THREADS = CPB * NQ;
-  static constexpr size_t bytes = sizeof(T) * ((size_t)THREADS * Cache<D>::NF + (size_t)CPB * 4 * D * NQ + 5 * (K + 1) * (K + 1));
+  static constexpr size_t bytes = sizeof(T) * ((size_t)THREADS * Cache<D>::NF + (size_t)CPB * NS * NQ + 5 * (K + 1) * (K + 1));
   static constexpr bool on = std::is_same<T, float>::value && bytes <= 48 * 1024;
 };
 
-// Four values of one point packed in 16-byte-aligned storage, so one sweep
-// tap is one vector shared-memory load (FP32: one 128-bit load for all four
-// fields instead of four 32-bit loads).
-template <typename T> struct alignas(16) P4 { T v[4]; };
-template <typename T> __device__ __forceinline__ P4<T> ld_p4(const P4<T>* p) { return *p; }
-template <> __device__ __forceinline__ P4<float> ld_p4<float>(const P4<float>* p) {
-  const float4 q = *reinterpret_cast<const float4*>(p);
-  P4<float> r;
-  r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
-  return r;
-}
-template <int NV, typename T> __device__ __forceinline__ void st_p4(P4<T>* p, const T* a) {
-  P4<T> r;
-#pragma unroll
-  for (int f = 0; f < 4; ++f) r.v[f] = f < NV ? a[f] : T(0);
-  *p = r;
-}
-
-// Sweep of a 1D matrix along one direction over a packed tile:
-// out[f] (+)= sum_j M[i_r][j] * tp[t with i_r := j].v[f]  (TRANS: M[j][i_r];
-// ACC: accumulate onto out).
-template <int N, int NFLD, bool TRANS, typename T, bool ACC = false>
-__device__ __forceinline__ void line_p4(const P4<T>* __restrict__ tp, int t, int ir, int stride, const T (*M)[N],
-                                        T* out) {
-  const int base = t - ir * stride;
-  if (!ACC) {
-#pragma unroll
-    for (int f = 0; f < NFLD; ++f) out[f] = T(0);
-  }
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
-    const T m = TRANS ? M[j][ir] : M[ir][j];
-    const P4<T> q = ld_p4(&tp[base + j * stride]);
-#pragma unroll
-    for (int f = 0; f < NFLD; ++f) out[f] = fma(m, q.v[f], out[f]);
-  }
-}
-
-// Shared memory of the cell Jacobian: per cell D planes of NQ packed points
-// (values: plane 0; Hessian sweeps and gradient fluxes: plane r holds the
-// direction-r entries of up to four fields).
 template <int D, int K, typename T, int CPB = CellCfg<D, K>::CPB>
 struct JacSmem {
-  static constexpr int N = K + 1, NQ = ipow(N, D);
+  static constexpr int N = K + 1, NQ = ipow(N, D), NS = (D + 1) * D;
   SmTab<N, T> st;
-  P4<T> tile[CPB][D * NQ];
+  T tile[CPB][NS * NQ];
   T stage[StageCfg<D, K, T, CPB>::on ? Cache<D>::NF * CPB * NQ : 1];
 };
 
@@ -186,7 +145,7 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_
   const int cl = threadIdx.x / NQ, t = threadIdx.x % NQ;
   const int64_t cell = blk * CPB + cl;
   const bool active = cell < nc;
-  P4<T>* tp = sm.tile[cl];
+  T* tile = sm.tile[cl];
   int ii[3] = {t % N, (t / N) % N, t / (N * N)};
   const int strd[3] = {1, N, N * N};
   constexpr bool STAGE = StageCfg<D, K, T, CPB>::on;
@@ -226,39 +185,46 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_
   // nodal -> Gauss values
 #pragma unroll
   for (int r = 0; r < D; ++r) {
-    st_p4<NF>(&tp[t], v);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) tile[f * NQ + t] = v[f];
     __syncthreads();
-    line_p4<N, NF, false>(tp, t, ii[r], strd[r], st.B, v);
+    line<D, N, NF, false>(tile, NQ, t, ii[r], strd[r], st.B, v);
     __syncthreads();
   }
   // reference gradients of all fields
   T dv[NF][D];
-  st_p4<NF>(&tp[t], v);
+#pragma unroll
+  for (int f = 0; f < NF; ++f) tile[f * NQ + t] = v[f];
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < D; ++r) {
     T o[NF];
-    line_p4<N, NF, false>(tp, t, ii[r], strd[r], st.Dg, o);
+    line<D, N, NF, false>(tile, NQ, t, ii[r], strd[r], st.Dg, o);
 #pragma unroll
     for (int f = 0; f < NF; ++f) dv[f][r] = o[f];
   }
   __syncthreads();
-  // reference Hessians of the velocity components: plane r holds d w_c / d xi_r
+  // reference Hessians of the velocity components
   T H[D][Sym<D>::n];
 #pragma unroll
-  for (int r = 0; r < D; ++r) {
-    T g[D];
+  for (int c = 0; c < D; ++c)
 #pragma unroll
-    for (int c = 0; c < D; ++c) g[c] = dv[c][r];
-    st_p4<D>(&tp[r * NQ + t], g);
-  }
+    for (int r = 0; r < D; ++r) tile[(c * D + r) * NQ + t] = dv[c][r];
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < Sym<D>::n; ++e) {
     const int r = sym_r(D, e), s = sym_s(D, e);
     T o[D];
-    // d/ds of (d w_c / d xi_r)
-    line_p4<N, D, false>(tp + r * NQ, t, ii[s], strd[s], st.Dg, o);
+    // d/ds of (d w_c / d xi_r): planes c*D + r
+    const int base = t - ii[s] * strd[s];
+#pragma unroll
+    for (int c = 0; c < D; ++c) o[c] = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      const T m = st.Dg[ii[s]][j];
+#pragma unroll
+      for (int c = 0; c < D; ++c) o[c] = fma(m, tile[(c * D + r) * NQ + base + j * strd[s]], o[c]);
+    }
 #pragma unroll
     for (int c = 0; c < D; ++c) H[c][e] = o[c];
   }
@@ -348,24 +314,29 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_
       Fx[D][r] = wt * s;
     }
   }
-  // ---- integrate: gradient fluxes through Dg^T (plane r: direction r of
-  // every field), then B^T to the nodes
+  // ---- integrate: gradient fluxes through Dg^T, then B^T to the nodes
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int r = 0; r < D; ++r) tile[(f * D + r) * NQ + t] = Fx[f][r];
+  __syncthreads();
 #pragma unroll
   for (int r = 0; r < D; ++r) {
-    T g[NF];
+    const int base = t - ii[r] * strd[r];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) g[f] = Fx[f][r];
-    st_p4<NF>(&tp[r * NQ + t], g);
+    for (int j = 0; j < N; ++j) {
+      const T m = st.Dg[j][ii[r]];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) fv[f] = fma(m, tile[(f * D + r) * NQ + base + j * strd[r]], fv[f]);
+    }
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < D; ++r) line_p4<N, NF, true, T, true>(tp + r * NQ, t, ii[r], strd[r], st.Dg, fv);
-  __syncthreads();
-#pragma unroll
   for (int r = 0; r < D; ++r) {
-    st_p4<NF>(&tp[t], fv);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) tile[f * NQ + t] = fv[f];
     __syncthreads();
-    line_p4<N, NF, true>(tp, t, ii[r], strd[r], st.B, fv);
+    line<D, N, NF, true>(tile, NQ, t, ii[r], strd[r], st.B, fv);
     __syncthreads();
   }
   if (active) {
