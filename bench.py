@@ -1,11 +1,15 @@
 """Benchmark: Jacobian-apply throughput of the rotor-stator operator on B300.
 
-Workload (default): 3D rotor-stator cylinder, 137,088 Q2 hexes (m=28, n_r=9,
-n_s=18, n_z=36), 4,546,148 DoFs, Re=200 (nu = 1/(400 pi), omega = 1), BDF2,
-dt = 0.005, rotor at theta = 0.137, smooth low-mode linearisation state,
-FP64.  One step = one full Jacobian apply y = J x (cell kernel, mortar face
-kernel, Dirichlet rows) with the per-point linearisation already cached.
-The working set (1.1 GB cache + vectors) exceeds the 126 MB L2.
+Workload (default, 3d_q2): 3D rotor-stator cylinder, 131,072 Q2 hexes (m=32,
+n_r=8, n_s=16, n_z=32), 4,359,940 DoFs, Re=200 (nu = 1/(400 pi), omega = 1),
+BDF2, dt = 0.005, rotor at theta = 0.137, smooth low-mode linearisation
+state, FP64.  One step = one full Jacobian apply y = J x (cell kernel, mortar
+face kernel, Dirichlet rows) with the per-point linearisation already cached.
+The working set (1.1 GB cache + vectors) exceeds the 126 MB L2.  Beside the
+headline: FP32 and double-float applies, residual, linearisation set-up, the
+end-to-end apply from host buffers, and (unless --no-solve) one Newton step
+to 1e-8 with the FP32 and the FP64 multigrid; --batched adds the 12-instance
+sweep (batched apply and batched Newton step), --transient N the BDF2 driver.
 
 Prints one JSON line.  --impl reference times the CPU FP64 oracle instead
 (matrix-free path on a bounded sample of cells and mortar cells).
