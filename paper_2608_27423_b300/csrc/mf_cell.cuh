@@ -285,13 +285,19 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_
       gal[c] = cv;
       Rl[c] = fma(-nu, l, cv + gr[c]);
     }
-    // physical flux of grad v: nu grad w - r I + tau (R' (x) a + R* (x) w)
+    // physical flux of grad v: nu grad w - r I + tau (R' (x) a + R* (x) w),
+    // with the quadrature weight W folded into its coefficients before the
+    // J^-1 contraction (W nu, W tau R', W tau R*, W r: fewer FP64 multiplies)
+    const T Wnu = Wq * nu, Wtau = Wq * tau, Wp = Wq * v[D];
+    T WRl[D], WRs[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) { WRl[c] = Wtau * Rl[c]; WRs[c] = Wtau * Rs[c]; }
     T Fp[D][D];
 #pragma unroll
     for (int c = 0; c < D; ++c)
 #pragma unroll
       for (int m = 0; m < D; ++m)
-        Fp[c][m] = fma(nu, gw[c][m], tau * fma(Rl[c], a[m], Rs[c] * v[m])) - (c == m ? v[D] : T(0));
+        Fp[c][m] = fma(Wnu, gw[c][m], fma(WRl[c], a[m], WRs[c] * v[m])) - (c == m ? Wp : T(0));
     T divw = T(0);
 #pragma unroll
     for (int c = 0; c < D; ++c) { fv[c] = Wq * gal[c]; divw += gw[c][c]; }
@@ -300,18 +306,17 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_
     for (int c = 0; c < D; ++c)
 #pragma unroll
       for (int r = 0; r < D; ++r) {
-        T s = T(0);
+        T s = Ji[r][0] * Fp[c][0];
 #pragma unroll
-        for (int m = 0; m < D; ++m) s = fma(Ji[r][m], Fp[c][m], s);
-        Fx[c][r] = Wq * s;
+        for (int m = 1; m < D; ++m) s = fma(Ji[r][m], Fp[c][m], s);
+        Fx[c][r] = s;
       }
-    const T wt = Wq * tau;
 #pragma unroll
     for (int r = 0; r < D; ++r) {
-      T s = T(0);
+      T s = Ji[r][0] * WRl[0];
 #pragma unroll
-      for (int m = 0; m < D; ++m) s = fma(Ji[r][m], Rl[m], s);
-      Fx[D][r] = wt * s;
+      for (int m = 1; m < D; ++m) s = fma(Ji[r][m], WRl[m], s);
+      Fx[D][r] = s;
     }
   }
   // ---- integrate: gradient fluxes through Dg^T, then B^T to the nodes
