@@ -136,6 +136,33 @@ mf_status mf_mesh_read(const mf_mesh* m, double* x0, uint8_t* node_side, uint8_t
                        uint8_t* cell_side, int32_t* iface_rotor, int32_t* iface_stator);
 mf_status mf_mesh_coarsen_map(const mf_mesh_params* fine, mf_mesh_params* coarse, int32_t* parent, uint8_t* child);
 
+/* ---------------------------------------------------------------- checkpoint / resume
+ * A time-dependent run (mf_run_transient or the caller's own BDF loop) is
+ * fully described by u^n, u^{n-1} (BDF2), the rotor angle and the step/time
+ * counters.  mf_checkpoint_write stores them in one file: a one-line JSON
+ * header (format "mf-checkpoint-1", d, k, sizes, an FNV-1a fingerprint of the
+ * mesh's cells, coordinates, sides and walls, bdf, step, t, theta, dt, nu,
+ * omega) followed by the raw little-endian FP64 arrays u^n and, for BDF2,
+ * u^{n-1}, each [n_nodes][d+1] in the library's layout.  The file is written
+ * to path.tmp and renamed, so an interrupted write leaves the old checkpoint.
+ * mf_checkpoint_read checks the format, the mesh fingerprint, the sizes and
+ * the file length, fills info and copies the arrays into u_n / u_nm1 (either
+ * may be NULL to read the header only).  Both take HOST buffers (copy device
+ * state to the host first) and touch no GPU.  Errors: MF_ERR_ARG (null
+ * pointers, bdf not 1/2, non-finite values, I/O failure, another mesh, a
+ * malformed or truncated file).  Not in the paper (no restart facility is
+ * described); it lets the 50-step transient of the large cylinder resume. */
+typedef struct {
+  int     bdf;      /* 1 or 2: number of state arrays stored */
+  int64_t step;     /* time steps taken */
+  double  t;        /* simulated time */
+  double  theta;    /* rotor angle at t */
+  double  dt, nu, omega;
+} mf_checkpoint_info;
+mf_status mf_checkpoint_write(const char* path, const mf_mesh* m, const mf_checkpoint_info* info, const double* u_n,
+                              const double* u_nm1);
+mf_status mf_checkpoint_read(const char* path, const mf_mesh* m, mf_checkpoint_info* info, double* u_n, double* u_nm1);
+
 /* ---------------------------------------------------------------- options */
 typedef struct {
   double penalty_F;   /* F of Eq. EqPenalty (default 1) */

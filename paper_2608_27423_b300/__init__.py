@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import MF_FP64, MF_FP32, MF_DF64, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
     MfSolverOpts, MfSolveReport
 
-__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
+__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
            "solver_defaults"]
 
 
@@ -123,6 +123,68 @@ def coarsen_map(**params):
     return {f: getattr(cp, f) for f, _ in _lib.MfMeshParams._fields_}, parent, child
 
 
+def _mesh_handle(mesh):
+    """An mf_mesh (host copy) of a mesh object; free it with mf_mesh_free."""
+    lib = _lib.load()
+    x0 = np.ascontiguousarray(mesh.x0, dtype=np.float64)
+    ns = np.ascontiguousarray(mesh.node_side, dtype=np.uint8)
+    wall = np.ascontiguousarray(mesh.wall, dtype=np.uint8)
+    cells = np.ascontiguousarray(mesh.cells, dtype=np.int32)
+    cs = np.ascontiguousarray(mesh.cell_side, dtype=np.uint8)
+    ifr = np.ascontiguousarray(mesh.iface_rotor, dtype=np.int32)
+    ifs = np.ascontiguousarray(mesh.iface_stator, dtype=np.int32)
+    mp = C.c_void_p()
+    _check(lib.mf_mesh_from_arrays(int(mesh.d), int(mesh.k), x0.shape[0], _np_ptr(x0), _np_ptr(ns), _np_ptr(wall),
+                                   cells.shape[0], _np_ptr(cells), _np_ptr(cs), float(mesh.R), int(mesh.n_R),
+                                   int(mesh.n_z), float(mesh.H), float(mesh.phi0), _np_ptr(ifr), _np_ptr(ifs),
+                                   C.byref(mp)), None, "mf_mesh_from_arrays")
+    return mp
+
+
+def _host_f64(a):
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def save_checkpoint(path, mesh, u_n, u_nm1=None, *, step, t, theta, dt, nu, omega):
+    """Write a checkpoint of a time-dependent run (mf_checkpoint_write): u_n
+    and, for BDF2, u_nm1 ([n_nodes, d+1], numpy arrays or tensors on any
+    device; copied to the host), step, time, rotor angle and parameters."""
+    lib = _lib.load()
+    info = _lib.MfCheckpointInfo(bdf=2 if u_nm1 is not None else 1, step=int(step), t=float(t), theta=float(theta),
+                                 dt=float(dt), nu=float(nu), omega=float(omega))
+    a = _host_f64(u_n)
+    b = _host_f64(u_nm1) if u_nm1 is not None else None
+    for arr in (a, b):
+        if arr is not None and arr.size != mesh.n_nodes * (mesh.d + 1):
+            raise MfError("save_checkpoint: state size does not match the mesh")
+    mp = _mesh_handle(mesh)
+    try:
+        st = lib.mf_checkpoint_write(str(path).encode(), mp, C.byref(info), _np_ptr(a),
+                                     _np_ptr(b) if b is not None else None)
+    finally:
+        lib.mf_mesh_free(mp)
+    _check(st, None, "mf_checkpoint_write")
+
+
+def load_checkpoint(path, mesh):
+    """Read a checkpoint written for `mesh` (mf_checkpoint_read).  Returns
+    (info dict, u_n, u_nm1 or None) with host numpy arrays [n_nodes, d+1]."""
+    lib = _lib.load()
+    info = _lib.MfCheckpointInfo()
+    shape = (mesh.n_nodes, mesh.d + 1)
+    a, b = np.empty(shape), np.empty(shape)
+    mp = _mesh_handle(mesh)
+    try:
+        st = lib.mf_checkpoint_read(str(path).encode(), mp, C.byref(info), _np_ptr(a), _np_ptr(b))
+    finally:
+        lib.mf_mesh_free(mp)
+    _check(st, None, "mf_checkpoint_read")
+    d = {f: getattr(info, f) for f, _ in _lib.MfCheckpointInfo._fields_}
+    return d, a, (b if info.bdf == 2 else None)
+
+
 class RotorStatorOperator:
     """One operator instance on the current CUDA device.
 
@@ -134,18 +196,7 @@ class RotorStatorOperator:
         lib = _lib.load()
         self.lib = lib
         self.d, self.k = int(mesh.d), int(mesh.k)
-        x0 = np.ascontiguousarray(mesh.x0, dtype=np.float64)
-        ns = np.ascontiguousarray(mesh.node_side, dtype=np.uint8)
-        wall = np.ascontiguousarray(mesh.wall, dtype=np.uint8)
-        cells = np.ascontiguousarray(mesh.cells, dtype=np.int32)
-        cs = np.ascontiguousarray(mesh.cell_side, dtype=np.uint8)
-        ifr = np.ascontiguousarray(mesh.iface_rotor, dtype=np.int32)
-        ifs = np.ascontiguousarray(mesh.iface_stator, dtype=np.int32)
-        mp = C.c_void_p()
-        _check(lib.mf_mesh_from_arrays(self.d, self.k, x0.shape[0], _np_ptr(x0), _np_ptr(ns), _np_ptr(wall),
-                                       cells.shape[0], _np_ptr(cells), _np_ptr(cs), float(mesh.R), int(mesh.n_R),
-                                       int(mesh.n_z), float(mesh.H), float(mesh.phi0), _np_ptr(ifr), _np_ptr(ifs),
-                                       C.byref(mp)), None, "mf_mesh_from_arrays")
+        mp = _mesh_handle(mesh)
         opt = _lib.MfOptions()
         opt.penalty_F = penalty_F
         hp = C.c_void_p()

@@ -324,6 +324,7 @@ extern "C" mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const do
 extern "C" void mf_mesh_free(mf_mesh* m) { delete m; }
 
 #include "mf_meshgen.inc"
+#include "mf_checkpoint.inc"
 
 // ------------------------------------------------------------------ create
 static void free_ws(Workspace& w) {
