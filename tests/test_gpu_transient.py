@@ -157,3 +157,34 @@ def test_transient_blades_move_with_the_rotor():
     assert abs(lo[1, 3] / rec["torque_moving"][-1] - 1) < 1e-12 and abs(lo[0, 3] - rec["torque_still"][-1]) < \
         1e-12 * abs(lo[1, 3])
     assert abs(lo[:, 4].sum() / rec["power"][-1] - 1) < 1e-12
+
+
+def test_checkpoint_resume_continues_the_run(tmp_path):
+    """Four BDF2 steps in one run equal two steps, a checkpoint written and
+    read back (mf_checkpoint_write / mf_checkpoint_read), and two more steps on
+    a freshly created operator started at the checkpoint's angle."""
+    from paper_2608_27423_b300 import solver_defaults, save_checkpoint, load_checkpoint, MF_PC_GMRES, MF_FP32
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    o = solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=30)
+    kw = dict(newton_iters=4, krylov_iters=15, opts=o)
+    theta0, dt, omega = 0.137, 0.005, 1.0
+    ops, mesh, u0, um1 = _spin_case(1)
+    un, unm1 = T(u0), T(um1)
+    ops[0].run_transient(un, unm1, 4, theta0, **kw)
+    ref = un.cpu().numpy()
+    ops, mesh, u0, um1 = _spin_case(1)
+    un, unm1 = T(u0), T(um1)
+    ops[0].run_transient(un, unm1, 2, theta0, **kw)
+    path = tmp_path / "spin.ckpt"
+    save_checkpoint(path, mesh, un, unm1, step=2, t=2 * dt, theta=theta0 + 2 * omega * dt, dt=dt,
+                    nu=1.0 / (2.0 * np.pi * 200.0), omega=omega)
+    del ops, un, unm1
+    ops, mesh, _, _ = _spin_case(1)                      # a new operator, as in a restarted process
+    info, a, b = load_checkpoint(path, mesh)
+    assert info["step"] == 2 and info["bdf"] == 2
+    un, unm1 = T(a), T(b)
+    ops[0].run_transient(un, unm1, 2, info["theta"], **kw)
+    got = un.cpu().numpy()
+    dv = np.linalg.norm(got[:, :3] - ref[:, :3]) / np.linalg.norm(ref[:, :3])
+    pa, pb = got[:, 3] - got[:, 3].mean(), ref[:, 3] - ref[:, 3].mean()
+    assert dv < 1e-6 and np.linalg.norm(pa - pb) / np.linalg.norm(pb) < 1e-5, dv
