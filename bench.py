@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--mg-levels", type=int, default=4)
     ap.add_argument("--batched", action="store_true", help="also time 12 uneven instances, batched vs one by one")
     ap.add_argument("--transient", type=int, default=0, help="also run this many graph-captured BDF2 time steps")
+    ap.add_argument("--transient-newton", type=int, default=3, help="Newton iterations per transient step")
+    ap.add_argument("--transient-krylov", type=int, default=8, help="FGMRES dimension per Newton iteration")
+    ap.add_argument("--transient-rest", action="store_true",
+                    help="start the transient from rest (u = 0; the blades and walls drive the flow)")
+    ap.add_argument("--transient-no-eager", action="store_true", help="time only the graph-replayed steps")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default cells per block (profiling runs: timings under ncu are not representative)")
     return ap.parse_args()
@@ -221,8 +226,9 @@ def solve_leg(args, op, mesh, prm, f, T):
 # --------------------------------------------------------------------- transient leg
 def transient_leg(args, op, mesh, prm, f, T):
     """BDF2 time steps with the rotor turning at omega (remap every step), each
-    step 3 Newton iterations x FGMRES(8) preconditioned by the FP32 multigrid
-    V-cycle; the step is captured once as a CUDA graph and replayed.  Reports
+    step a fixed number of Newton iterations x FGMRES(m) (default 3 x 8)
+    preconditioned by the FP32 multigrid V-cycle; the step is captured once as
+    a CUDA graph and replayed.  Reports
     the time per step (graph vs eager), DoFs/s over the steps, the histories
     of kinetic energy, viscous dissipation, impeller torque and wall power,
     and the per-step residual reductions."""
@@ -234,15 +240,19 @@ def transient_leg(args, op, mesh, prm, f, T):
     if op.__dict__.get("_coarse") is None:
         build_levels(op, cfg, prm, args.mg_levels - 1)
     u0 = np.zeros_like(f["up_star"])
-    u0[:, :d] = f["u_n"]
-    u0[mesh.wall.astype(bool), :d] = 0.0
+    if not args.transient_rest:
+        u0[:, :d] = f["u_n"]
+        u0[mesh.wall.astype(bool), :d] = 0.0
     o = solver_defaults(pc=MF_PC_MG, pc_precision=MF_FP32, mg_smooth=4, mg_coarse_iters=40)
-    out = {"steps": args.transient, "newton_per_step": 3, "fgmres_per_newton": 8}
-    for label, graph in (("graph", True), ("eager", False)):
+    nn, nk = args.transient_newton, args.transient_krylov
+    out = {"steps": args.transient, "newton_per_step": nn, "fgmres_per_newton": nk,
+           "start": "rest" if args.transient_rest else "smooth random u^n (walls zero)"}
+    modes = (("graph", True),) if args.transient_no_eager else (("graph", True), ("eager", False))
+    for label, graph in modes:
         un, unm1 = T(u0), T(u0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        rec = op.run_transient(un, unm1, args.transient, prm["theta"], newton_iters=3, krylov_iters=8, opts=o,
+        rec = op.run_transient(un, unm1, args.transient, prm["theta"], newton_iters=nn, krylov_iters=nk, opts=o,
                                use_graph=graph)
         torch.cuda.synchronize()
         dt_s = time.perf_counter() - t0
