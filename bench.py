@@ -30,9 +30,9 @@ sys.path.insert(0, ROOT)
 METRIC = "Jacobian-apply DoFs/s (FP64 vs FP32) at Q2/Q3; time to 1e-8 residual per step"
 FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (non-tensor) nominal
 FP64_PROBE_TFLOPS = 1.128        # FMA-chain probe on the B300s
-# DRAM bytes (read + write) per cell of k_cell_jac<3,2,double> from one ncu capture on the 16,384-hex
-# cylinder (profiles/k_cell_jac_fp64_3d_q2_mid.md: 134.845 MB + 4.531 MB); traffic scales with the cells.
-TRAFFIC_BYTES_PER_CELL_Q2_3D_FP64 = (134.844928e6 + 4.531456e6) / 16384
+# DRAM bytes (read + write) per cell of k_cell_jac<3,2,double,9> from one ncu capture on the 16,384-hex
+# cylinder (profiles/k_cell_jac_fp64_3d_q2_mid.md: 134.740 MB + 4.888 MB); traffic scales with the cells.
+TRAFFIC_BYTES_PER_CELL_Q2_3D_FP64 = (134.739968e6 + 4.887808e6) / 16384
 
 
 def parse():
