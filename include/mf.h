@@ -136,6 +136,17 @@ mf_status mf_mesh_read(const mf_mesh* m, double* x0, uint8_t* node_side, uint8_t
                        uint8_t* cell_side, int32_t* iface_rotor, int32_t* iface_stator);
 mf_status mf_mesh_coarsen_map(const mf_mesh_params* fine, mf_mesh_params* coarse, int32_t* parent, uint8_t* child);
 
+/* ---------------------------------------------------------------- per-call metrics log
+ * mf_log_open(path): from now on the mesh generator, mf_solve_step,
+ * mf_batch_solve_step, mf_run_transient, mf_autotune and the checkpoint calls
+ * each append one JSON object per line to `path` (created if missing): the
+ * call name, its status, sizes, iteration counts, the residual history of a
+ * solve and the wall seconds.  NULL or "" turns the log off (the default).
+ * Process-wide; records of concurrent calls are written whole (a mutex).
+ * MF_ERR_ARG when the file cannot be opened for appending.  Not in the paper
+ * (the paper reports iteration counts and wall times per run). */
+mf_status mf_log_open(const char* path);
+
 /* ---------------------------------------------------------------- checkpoint / resume
  * A time-dependent run (mf_run_transient or the caller's own BDF loop) is
  * fully described by u^n, u^{n-1} (BDF2), the rotor angle and the step/time

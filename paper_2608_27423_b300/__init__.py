@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import MF_FP64, MF_FP32, MF_DF64, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
     MfSolverOpts, MfSolveReport
 
-__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
+__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "log_open", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
            "solver_defaults"]
 
 
@@ -139,6 +139,12 @@ def _mesh_handle(mesh):
                                    int(mesh.n_z), float(mesh.H), float(mesh.phi0), _np_ptr(ifr), _np_ptr(ifs),
                                    C.byref(mp)), None, "mf_mesh_from_arrays")
     return mp
+
+
+def log_open(path):
+    """Append one JSON line per library call (solves, transient runs, mesh
+    generation, autotuning, checkpoints) to `path`; None turns the log off."""
+    _check(_lib.load().mf_log_open(str(path).encode() if path else None), None, "mf_log_open")
 
 
 def _host_f64(a):

@@ -20,6 +20,8 @@
 
 using namespace mf;
 
+#include "mf_log.inc"
+
 struct mf_mesh {
   int d, k;
   int64_t nn, nc;

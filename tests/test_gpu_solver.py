@@ -132,3 +132,31 @@ def test_2d_workload_jacobi_newton_to_1e10():
     assert rep.res_norm[rep.newton_iters] <= 1e-10 * rep.res_norm[0]
     du, dp = _compare(up, ref)
     assert du < 1e-7 and dp < 1e-5, (du, dp)
+
+
+def test_metrics_log_records_solves(case, tmp_path):
+    """With mf_log_open set, mf_solve_step and mf_run_transient append one JSON
+    line each; the solve's line carries the report's residual history."""
+    import json
+    import torch as _t
+    from paper_2608_27423_b300 import log_open, MF_PC_JACOBI, MF_FP64, solver_defaults
+    mesh, prm, f = case
+    path = tmp_path / "calls.jsonl"
+    log_open(path)
+    try:
+        st, rep, up = _solve_gpu(mesh, prm, f, pc=MF_PC_JACOBI, pc_precision=MF_FP64, newton_rtol=1e-8,
+                                 lin_rtol=1e-6, max_newton=20, restart=80, max_lin_iters=2000)
+        from paper_2608_27423_b300 import RotorStatorOperator, MF_PC_GMRES, MF_FP32
+        g = RotorStatorOperator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
+        un = _t.tensor(np.ascontiguousarray(f["u_n_full"]), dtype=_t.float64, device="cuda")
+        g.run_transient(un, None, 2, prm["theta"], newton_iters=2, krylov_iters=6,
+                        opts=solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=10))
+    finally:
+        log_open(None)
+    recs = [json.loads(line) for line in open(path)]
+    calls = [r["call"] for r in recs]
+    assert calls == ["mf_solve_step", "mf_run_transient"], calls
+    s = recs[0]
+    assert s["status"] == st == 0 and s["newton_iters"] == rep.newton_iters and s["n_dofs"] == mesh.n_dofs
+    assert np.allclose(s["res_norm"], list(rep.res_norm[:rep.newton_iters + 1]), rtol=1e-15)
+    assert recs[1]["n_steps"] == 2 and recs[1]["graph"] == 1 and recs[1]["theta_end"] > recs[1]["theta0"]
