@@ -414,40 +414,39 @@ def _oracle_worker(job):
     (one BLAS thread), and the mortar build + apply of z-layer `layer`.
     Returns (cells done, volume seconds, mortar seconds for one layer)."""
     name, lo, hi, layer, budget = job
-    from threadpoolctl import threadpool_limits
-    with threadpool_limits(1):
-        mesh, prm, f = synth.make_config(name)
-        from oracle.fem import Problem
-        from oracle.mortar import Mortar
-        prob = Problem(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"], prm["theta"])
-        prob.set_history(f["u_n"], f["u_nm1"])
-        d = mesh.d
-        xc = f["x"].copy()
-        xc[mesh.wall.astype(bool), :d] = 0.0
-        out = np.zeros((mesh.n_nodes, d + 1))
-        t_vol, done = 0.0, lo
-        while t_vol < budget and done < hi:
-            cl = np.arange(done, min(hi, done + 256))
-            t0 = time.perf_counter()
-            prob.volume_apply(f["up_star"], xc, cl=cl, out=out)
-            t_vol += time.perf_counter() - t0
-            done += len(cl)
-        t_mort = 0.0
-        if layer is not None and d == 3:
-            class OneLayer:
-                pass
-            m1 = OneLayer()
-            for key in ("d", "k", "x0", "cells", "cell_side", "node_side", "wall", "R", "n_R", "phi0"):
-                setattr(m1, key, getattr(mesh, key))
-            m1.n_z, m1.H = 1, mesh.H / mesh.n_z
-            m1.iface_rotor = mesh.iface_rotor[layer:layer + 1]
-            m1.iface_stator = mesh.iface_stator[layer:layer + 1]
-            prob.mesh = m1
-            t0 = time.perf_counter()
-            mt = Mortar.__new__(Mortar)
-            Mortar.__init__(mt, prob)
-            mt.apply(xc, out=out)
-            t_mort = time.perf_counter() - t0
+    # one BLAS thread: set in the environment this process was spawned with
+    mesh, prm, f = synth.make_config(name)
+    from oracle.fem import Problem
+    from oracle.mortar import Mortar
+    prob = Problem(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"], prm["theta"])
+    prob.set_history(f["u_n"], f["u_nm1"])
+    d = mesh.d
+    xc = f["x"].copy()
+    xc[mesh.wall.astype(bool), :d] = 0.0
+    out = np.zeros((mesh.n_nodes, d + 1))
+    t_vol, done = 0.0, lo
+    while t_vol < budget and done < hi:
+        cl = np.arange(done, min(hi, done + 256))
+        t0 = time.perf_counter()
+        prob.volume_apply(f["up_star"], xc, cl=cl, out=out)
+        t_vol += time.perf_counter() - t0
+        done += len(cl)
+    t_mort = 0.0
+    if layer is not None and d == 3:
+        class OneLayer:
+            pass
+        m1 = OneLayer()
+        for key in ("d", "k", "x0", "cells", "cell_side", "node_side", "wall", "R", "n_R", "phi0"):
+            setattr(m1, key, getattr(mesh, key))
+        m1.n_z, m1.H = 1, mesh.H / mesh.n_z
+        m1.iface_rotor = mesh.iface_rotor[layer:layer + 1]
+        m1.iface_stator = mesh.iface_stator[layer:layer + 1]
+        prob.mesh = m1
+        t0 = time.perf_counter()
+        mt = Mortar.__new__(Mortar)
+        Mortar.__init__(mt, prob)
+        mt.apply(xc, out=out)
+        t_mort = time.perf_counter() - t0
     return done - lo, t_vol, t_mort
 
 
@@ -473,8 +472,19 @@ def cpu_oracle_rate_all_cores(name, seconds, procs=None):
     edges = np.linspace(0, nc, procs + 1).astype(int)
     jobs = [(name, int(edges[i]), int(edges[i + 1]), (i % n_z) if mesh.d == 3 else None, 0.8 * seconds)
             for i in range(procs)]
-    with cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
-        res = list(ex.map(_oracle_worker, jobs))
+    # spawned workers start their BLAS with one thread (the variables are read when numpy loads)
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
+            res = list(ex.map(_oracle_worker, jobs))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     cells = sum(r[0] for r in res)
     t_vol = max(r[1] for r in res)
     t_layer = float(np.mean([r[2] for r in res])) if mesh.d == 3 else 0.0
