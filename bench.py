@@ -408,90 +408,117 @@ def cpu_oracle_rate(mesh, prm, f, seconds):
     return rate, sample, t_full
 
 
+_ORACLE_STATE = {}      # per worker process: workload -> (mesh, prm, fields, oracle problem, x, out, mortar s)
+_WORKLOAD_SIZES = {}    # parent process: workload -> (n_cells, n_z, d, n_dofs)
+
+
+def _oracle_state(name, layer):
+    """The worker's oracle set-up for `name`, built once per process: mesh and
+    fields, the volume problem, the test vector with zero wall velocities, and
+    the time to build and apply the mortar of z-layer `layer` (measured once)."""
+    if name not in _ORACLE_STATE:
+        mesh, prm, f = synth.make_config(name)
+        from oracle.fem import Problem
+        from oracle.mortar import Mortar
+        prob = Problem(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"], prm["theta"])
+        prob.set_history(f["u_n"], f["u_nm1"])
+        d = mesh.d
+        xc = f["x"].copy()
+        xc[mesh.wall.astype(bool), :d] = 0.0
+        out = np.zeros((mesh.n_nodes, d + 1))
+        t_mort = 0.0
+        if layer is not None and d == 3:
+            class OneLayer:
+                pass
+            m1 = OneLayer()
+            for key in ("d", "k", "x0", "cells", "cell_side", "node_side", "wall", "R", "n_R", "phi0"):
+                setattr(m1, key, getattr(mesh, key))
+            m1.n_z, m1.H = 1, mesh.H / mesh.n_z
+            m1.iface_rotor = mesh.iface_rotor[layer:layer + 1]
+            m1.iface_stator = mesh.iface_stator[layer:layer + 1]
+            vol_mesh, prob.mesh = prob.mesh, m1
+            t0 = time.perf_counter()
+            mt = Mortar.__new__(Mortar)
+            Mortar.__init__(mt, prob)
+            mt.apply(xc, out=out)
+            t_mort = time.perf_counter() - t0
+            prob.mesh = vol_mesh
+        _ORACLE_STATE[name] = (mesh, prm, f, prob, xc, out, t_mort)
+    return _ORACLE_STATE[name]
+
+
 def _oracle_worker(job):
     """One host process of the all-cores oracle timing: the oracle's
-    matrix-free volume apply on the cells [lo, hi) for about `budget` seconds
-    (one BLAS thread), and the mortar build + apply of z-layer `layer`.
-    Returns (cells done, volume seconds, mortar seconds for one layer)."""
+    matrix-free volume apply on cells from [lo, hi) for about `budget`
+    seconds (one BLAS thread, from the environment the process was spawned
+    with).  Returns (cells done, volume seconds, mortar seconds per layer)."""
     name, lo, hi, layer, budget = job
-    # one BLAS thread: set in the environment this process was spawned with
-    mesh, prm, f = synth.make_config(name)
-    from oracle.fem import Problem
-    from oracle.mortar import Mortar
-    prob = Problem(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"], prm["theta"])
-    prob.set_history(f["u_n"], f["u_nm1"])
-    d = mesh.d
-    xc = f["x"].copy()
-    xc[mesh.wall.astype(bool), :d] = 0.0
-    out = np.zeros((mesh.n_nodes, d + 1))
+    mesh, prm, f, prob, xc, out, t_mort = _oracle_state(name, layer)
     t_vol, done = 0.0, lo
     while t_vol < budget and done < hi:
-        cl = np.arange(done, min(hi, done + 256))
+        cl = np.arange(done, min(hi, done + 64))
         t0 = time.perf_counter()
         prob.volume_apply(f["up_star"], xc, cl=cl, out=out)
         t_vol += time.perf_counter() - t0
         done += len(cl)
-    t_mort = 0.0
-    if layer is not None and d == 3:
-        class OneLayer:
-            pass
-        m1 = OneLayer()
-        for key in ("d", "k", "x0", "cells", "cell_side", "node_side", "wall", "R", "n_R", "phi0"):
-            setattr(m1, key, getattr(mesh, key))
-        m1.n_z, m1.H = 1, mesh.H / mesh.n_z
-        m1.iface_rotor = mesh.iface_rotor[layer:layer + 1]
-        m1.iface_stator = mesh.iface_stator[layer:layer + 1]
-        prob.mesh = m1
-        t0 = time.perf_counter()
-        mt = Mortar.__new__(Mortar)
-        Mortar.__init__(mt, prob)
-        mt.apply(xc, out=out)
-        t_mort = time.perf_counter() - t0
     return done - lo, t_vol, t_mort
 
 
-def cpu_oracle_rate_all_cores(name, seconds, procs=None):
-    """The oracle's matrix-free apply on the host cores: one spawned process
-    per core (at most 32; one BLAS thread each) applies the volume terms to its own
-    contiguous slice of cells for about `seconds`, and builds + applies the
-    mortar of one z-layer.  Whole-operator time = all cells at the measured
-    aggregate cell rate + the z-layers' mortar work spread over the processes."""
+def oracle_pool(procs=None):
+    """A pool of spawned oracle processes (one per core, at most 32 and at most
+    one per 3 GB of free host memory), each with one BLAS thread."""
     import concurrent.futures as cf
     import multiprocessing as mp
     if not procs:
-        # one process per core, at most 32 and at most one per 3 GB of free host memory (each holds the
-        # workload's mesh, fields and oracle state)
         procs = min(os.cpu_count() or 1, 32)
         try:
             import psutil
             procs = max(1, min(procs, int(psutil.virtual_memory().available // (3 << 30))))
         except Exception:
             pass
-    mesh, prm, f = synth.make_config(name)
-    nc, n_z = mesh.n_cells, mesh.n_z
-    edges = np.linspace(0, nc, procs + 1).astype(int)
-    jobs = [(name, int(edges[i]), int(edges[i + 1]), (i % n_z) if mesh.d == 3 else None, 0.8 * seconds)
-            for i in range(procs)]
-    # spawned workers start their BLAS with one thread (the variables are read when numpy loads)
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
     saved = {k: os.environ.get(k) for k in keys}
-    os.environ.update({k: "1" for k in keys})
+    os.environ.update({k: "1" for k in keys})          # read by numpy as each worker starts
     try:
-        with cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn")) as ex:
-            res = list(ex.map(_oracle_worker, jobs))
+        ex = cf.ProcessPoolExecutor(max_workers=procs, mp_context=mp.get_context("spawn"))
     finally:
         for k, v in saved.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
+    return ex, procs
+
+
+def cpu_oracle_rate_all_cores(name, seconds, pool=None):
+    """The oracle's matrix-free apply on the host cores: every process of the
+    pool applies the volume terms to its own contiguous slice of cells for
+    about `seconds` (the first call per process also builds its workload and
+    times one z-layer's mortar).  Aggregate rate = processes x (cells / volume
+    seconds, summed over processes); whole-operator time = all cells at that
+    rate + the z-layers' mortar work spread over the processes."""
+    own = pool is None
+    ex, procs = oracle_pool() if own else pool
+    try:
+        if name not in _WORKLOAD_SIZES:
+            mesh = synth.make_config(name)[0]
+            _WORKLOAD_SIZES[name] = (mesh.n_cells, mesh.n_z, mesh.d, mesh.n_dofs)
+        nc, n_z, d, n_dofs = _WORKLOAD_SIZES[name]
+        edges = np.linspace(0, nc, procs + 1).astype(int)
+        jobs = [(name, int(edges[i]), int(edges[i + 1]), (i % n_z) if d == 3 else None, seconds)
+                for i in range(procs)]
+        res = list(ex.map(_oracle_worker, jobs))
+    finally:
+        if own:
+            ex.shutdown()
     cells = sum(r[0] for r in res)
-    t_vol = max(r[1] for r in res)
-    t_layer = float(np.mean([r[2] for r in res])) if mesh.d == 3 else 0.0
-    t_full = nc * t_vol / cells + -(-n_z // procs) * t_layer
-    sample = (f"{procs} processes x 1 thread: volume apply on {cells} of {nc} cells in {t_vol:.1f} s (aggregate), "
+    t_sum = sum(r[1] for r in res)
+    rate_cells = procs * cells / t_sum
+    t_layer = float(np.mean([r[2] for r in res])) if d == 3 else 0.0
+    t_full = nc / rate_cells + -(-n_z // procs) * t_layer
+    sample = (f"{procs} processes x 1 thread: volume apply on {cells} of {nc} cells ({t_sum:.1f} process-seconds), "
               f"mortar build and apply of one z-layer per process ({t_layer:.2f} s), scaled to the whole operator")
-    return mesh.n_dofs / t_full, sample, procs
+    return n_dofs / t_full, sample, procs
 
 
 def cpu_oracle_2d():
@@ -677,7 +704,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         rate1, sample1, _ = cpu_oracle_rate(mesh, prm, f, args.cpu_seconds)
         try:
-            rate, sample, procs = cpu_oracle_rate_all_cores(args.workload, args.cpu_seconds)
+            pool = oracle_pool()
+            try:
+                cpu_oracle_rate_all_cores(args.workload, 0.5, pool)        # workers build the workload
+                rate, sample, procs = cpu_oracle_rate_all_cores(args.workload, args.cpu_seconds, pool)
+            finally:
+                pool[0].shutdown()
         except Exception as exc:     # keep the bench line: report the single-process timing
             rate, sample, procs = rate1, f"{sample1} (all-cores timing failed: {exc!r})", cpu_cores_used()
         line["cpu_baseline"] = {"value": rate, "unit": "DoFs/s", "cores": procs, "kind": "oracle",
@@ -695,14 +727,20 @@ def main_reference(args, rank, world):
     if rank != 0:
         return
     mesh, prm, f = build_inputs(args.workload)
-    budget = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    # one pool for the whole run: the workers build the workload once (first warm-up step), then every step
+    # is a bounded sample; the run stays within a few minutes for any --steps
+    budget = max(0.2, 120.0 / max(1, args.steps + args.warmup))
     rates = []
     sample = ""
-    cores = 1
-    for i in range(args.warmup + args.steps):
-        rate, sample, cores = cpu_oracle_rate_all_cores(args.workload, budget)
-        if i >= args.warmup:
-            rates.append(rate)
+    pool = oracle_pool()
+    cores = pool[1]
+    try:
+        for i in range(max(1, args.warmup) + args.steps):
+            rate, sample, cores = cpu_oracle_rate_all_cores(args.workload, budget, pool)
+            if i >= max(1, args.warmup):
+                rates.append(rate)
+    finally:
+        pool[0].shutdown()
     value = float(np.median(rates))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mesh.n_dofs / value * 1e3,
