@@ -59,3 +59,30 @@ def test_generator_rejects_bad_parameters():
         coarsen_map(d=2, k=2, m=3, n_r=2, n_s=2)
     with pytest.raises(TypeError):
         rotor_stator_mesh(radius=1.0)
+
+
+def _node_count(d, k, m, n_r, n_s, n_z):
+    """Nodes of the generated mesh: O-grid square, rotor rings, stator rings
+    (interface duplicated), times the node layers in z."""
+    mk, nRk = m * k, 4 * m * k
+    n2 = (mk + 1) ** 2 + n_r * k * nRk + (n_s * k + 1) * nRk
+    return n2 * (n_z * k + 1 if d == 3 else 1)
+
+
+def test_dof_per_cell_ratio_matches_the_papers_meshes():
+    """Table of the paper's scalability meshes (Section 4.3): DoFs / cells is
+    32.2-33.1 at Q2Q2 and 105-110 at Q3Q3 (d+1 fields on k^3 nodes per cell plus
+    surface terms); the synthetic cylinders of the workloads fall in the same
+    band.  The node-count formula is checked against the generator first."""
+    from paper_2608_27423_b300 import rotor_stator_mesh
+    from synth.configs import CONFIGS
+    for p in (dict(d=3, k=2, m=4, n_r=2, n_s=2, n_z=3), dict(d=3, k=3, m=6, n_r=3, n_s=2, n_z=5),
+              dict(d=2, k=2, m=16, n_r=5, n_s=12, n_z=1)):
+        assert rotor_stator_mesh(**p).n_nodes == _node_count(**p)
+    bands = {2: (32.0, 34.0), 3: (105.0, 113.0)}
+    for name in ("3d_q2", "3d_q3", "3d_q3_1m"):
+        c = CONFIGS[name]
+        cells = (c["m"] ** 2 + 4 * c["m"] * (c["n_r"] + c["n_s"])) * c["n_z"]
+        dofs = 4 * _node_count(3, c["k"], c["m"], c["n_r"], c["n_s"], c["n_z"])
+        lo, hi = bands[c["k"]]
+        assert lo <= dofs / cells <= hi, (name, cells, dofs, dofs / cells)
