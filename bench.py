@@ -427,7 +427,12 @@ def _oracle_state(name, layer):
         xc[mesh.wall.astype(bool), :d] = 0.0
         out = np.zeros((mesh.n_nodes, d + 1))
         t_mort = 0.0
-        if layer is not None and d == 3:
+        if d == 2:                      # one interface ring: the whole mortar
+            t0 = time.perf_counter()
+            mt = Mortar(prob)
+            mt.apply(xc, out=out)
+            t_mort = time.perf_counter() - t0
+        elif layer is not None:
             class OneLayer:
                 pass
             m1 = OneLayer()
@@ -505,8 +510,7 @@ def cpu_oracle_rate_all_cores(name, seconds, pool=None):
             _WORKLOAD_SIZES[name] = (mesh.n_cells, mesh.n_z, mesh.d, mesh.n_dofs)
         nc, n_z, d, n_dofs = _WORKLOAD_SIZES[name]
         edges = np.linspace(0, nc, procs + 1).astype(int)
-        jobs = [(name, int(edges[i]), int(edges[i + 1]), (i % n_z) if d == 3 else None, seconds)
-                for i in range(procs)]
+        jobs = [(name, int(edges[i]), int(edges[i + 1]), i % n_z, seconds) for i in range(procs)]
         res = list(ex.map(_oracle_worker, jobs))
     finally:
         if own:
@@ -514,7 +518,7 @@ def cpu_oracle_rate_all_cores(name, seconds, pool=None):
     cells = sum(r[0] for r in res)
     t_sum = sum(r[1] for r in res)
     rate_cells = procs * cells / t_sum
-    t_layer = float(np.mean([r[2] for r in res])) if d == 3 else 0.0
+    t_layer = float(np.mean([r[2] for r in res]))
     t_full = nc / rate_cells + -(-n_z // procs) * t_layer
     sample = (f"{procs} processes x 1 thread: volume apply on {cells} of {nc} cells ({t_sum:.1f} process-seconds), "
               f"mortar build and apply of one z-layer per process ({t_layer:.2f} s), scaled to the whole operator")
