@@ -77,7 +77,7 @@ template <typename T> __device__ __forceinline__ typename IO<T>::type to_io(T x)
 template <> __device__ __forceinline__ double to_io<df>(df x) { return x.to_double(); }
 
 // split a double array into df pairs (hi, lo)
-__global__ inline void k_split_df(const double* __restrict__ a, df* __restrict__ b, int64_t n) {
+__global__ void k_split_df(const double* __restrict__ a, df* __restrict__ b, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = df(a[i]);
 }
