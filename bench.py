@@ -590,11 +590,15 @@ def main():
     n_dofs = op.n_dofs
     d, k = mesh.d, mesh.k
     # launch shape of the cell Jacobian picked by measurement (cells per block, FP64 and FP32)
+    default_tune = {p: {"cells_per_block": [], "ms": [], "chosen": 9 if k == 2 else 4, "from_cache": False}
+                    for p in ("fp64", "fp32")}
     if args.no_autotune:
-        tune = {p: {"cells_per_block": [], "ms": [], "chosen": 9 if k == 2 else 4, "from_cache": False}
-                for p in ("fp64", "fp32")}
+        tune = default_tune
     else:
-        tune = op.autotune()
+        try:
+            tune = op.autotune()
+        except Exception as exc:         # keep the defaults and the bench line
+            tune = dict(default_tune, error=repr(exc))
 
     def timed(fn, steps, warm):
         for _ in range(warm):
@@ -684,14 +688,21 @@ def main():
            "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(yh.numel() * 8)}
 
     # ---- nonlinear step to 1e-8: all-FP64 vs mixed precision (same algorithm)
-    if not args.no_solve:
-        extra["solve_to_1e-8"] = solve_leg(args, op, mesh, prm, f, T)
-        op.set_linearization(up_star, prm["theta"])
+    # optional legs: a failure is reported in the line instead of losing the line
+    def leg(key, fn):
+        try:
+            extra[key] = fn()
+        except Exception as exc:
+            extra[key] = {"error": repr(exc)}
+            print(f"{key} failed: {exc!r}", file=sys.stderr, flush=True)
 
+    if not args.no_solve:
+        leg("solve_to_1e-8", lambda: solve_leg(args, op, mesh, prm, f, T))
+        op.set_linearization(up_star, prm["theta"])
     if args.batched:
-        extra["batched_12"] = batched_leg(args, T, dev)
+        leg("batched_12", lambda: batched_leg(args, T, dev))
     if args.transient > 0:
-        extra["transient"] = transient_leg(args, op, mesh, prm, f, T)
+        leg("transient", lambda: transient_leg(args, op, mesh, prm, f, T))
 
     line = {"metric": METRIC, "value": value, "unit": "DoFs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
