@@ -380,22 +380,9 @@ def cpu_oracle_rate(mesh, prm, f, seconds):
         prob.volume_apply(f["up_star"], xc, cl=cl, out=out)
         t_vol += time.perf_counter() - t0
         cells_done += len(cl)
-    # mortar: one z-layer of mortar cells
-    class OneLayer:
-        pass
-    m1 = OneLayer()
-    for key in ("d", "k", "x0", "cells", "cell_side", "node_side", "wall", "R", "n_R", "H", "phi0"):
-        setattr(m1, key, getattr(mesh, key))
-    m1.n_z = mesh.n_z
-    m1.iface_rotor = mesh.iface_rotor
-    m1.iface_stator = mesh.iface_stator
-    prob.mesh = m1
-    mt = Mortar.__new__(Mortar)
-    # set up only layer 0 of the mortar (same code path as Mortar.__init__ with n_z = 1); the set-up is the
-    # counterpart of the GPU's set_linearization and is not timed, like the GPU's
-    m1.n_z = 1
-    m1.H = mesh.H / mesh.n_z
-    Mortar.__init__(mt, prob)
+    # mortar: one z-layer of mortar cells (whole mortar in 2D); its set-up is the counterpart of the GPU's
+    # set_linearization and is not timed, like the GPU's
+    mt = _layer_mortar(prob, mesh, 0) if mesh.d == 3 else Mortar(prob)
     t0 = time.perf_counter()
     mt.apply(xc, out=out)
     t_mort = time.perf_counter() - t0
@@ -405,6 +392,28 @@ def cpu_oracle_rate(mesh, prm, f, seconds):
     sample = (f"volume apply on {cells_done} of {nc} cells ({t_vol:.1f} s) + mortar apply on 1 of "
               f"{n_layers} z-layers ({t_mort:.2f} s; its set-up untimed), scaled to the whole operator")
     return rate, sample, t_full
+
+
+def _layer_mortar(prob, mesh, layer):
+    """The oracle's mortar of one z-layer of a 3D mesh (the same code path as a
+    whole-mesh Mortar with n_z = 1), built on `prob`; prob.mesh is restored."""
+    from oracle.mortar import Mortar
+
+    class OneLayer:
+        pass
+    m1 = OneLayer()
+    for key in ("d", "k", "x0", "cells", "cell_side", "node_side", "wall", "R", "n_R", "phi0"):
+        setattr(m1, key, getattr(mesh, key))
+    m1.n_z, m1.H = 1, mesh.H / mesh.n_z
+    m1.iface_rotor = mesh.iface_rotor[layer:layer + 1]
+    m1.iface_stator = mesh.iface_stator[layer:layer + 1]
+    vol_mesh, prob.mesh = prob.mesh, m1
+    try:
+        mt = Mortar.__new__(Mortar)
+        Mortar.__init__(mt, prob)
+    finally:
+        prob.mesh = vol_mesh
+    return mt
 
 
 _ORACLE_STATE = {}      # per worker process: workload -> (mesh, prm, fields, oracle problem, x, out, mortar s)
@@ -432,21 +441,10 @@ def _oracle_state(name, layer):
             mt.apply(xc, out=out)
             t_mort = time.perf_counter() - t0
         elif layer is not None:
-            class OneLayer:
-                pass
-            m1 = OneLayer()
-            for key in ("d", "k", "x0", "cells", "cell_side", "node_side", "wall", "R", "n_R", "phi0"):
-                setattr(m1, key, getattr(mesh, key))
-            m1.n_z, m1.H = 1, mesh.H / mesh.n_z
-            m1.iface_rotor = mesh.iface_rotor[layer:layer + 1]
-            m1.iface_stator = mesh.iface_stator[layer:layer + 1]
-            vol_mesh, prob.mesh = prob.mesh, m1
-            mt = Mortar.__new__(Mortar)
-            Mortar.__init__(mt, prob)          # set-up of the layer's mortar points: untimed, like the GPU's
+            mt = _layer_mortar(prob, mesh, layer)    # set-up of the layer's mortar points: untimed, like the GPU's
             t0 = time.perf_counter()
             mt.apply(xc, out=out)
             t_mort = time.perf_counter() - t0
-            prob.mesh = vol_mesh
         _ORACLE_STATE[name] = (mesh, prm, f, prob, xc, out, t_mort)
     return _ORACLE_STATE[name]
 
