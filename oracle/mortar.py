@@ -18,15 +18,17 @@ import numpy as np
 from .basis import tensor_basis, gauss_rule, tensor_gauss
 
 
-def mortar_segments(theta, n_R):
+def mortar_segments(theta, n_R, n_Rs=None):
     """Sorted union of rotor vertices theta + 2 pi i / n_R and stator vertices
-    2 pi i / n_R on the circle (angles relative to the partition origin phi0).
-    Returns (start angle, length, rotor cell index, stator cell index) for every
-    piece of positive length."""
+    2 pi j / n_Rs (n_Rs = n_R: the paper's equal partitions) on the circle,
+    angles relative to the partition origin phi0.  Returns (start angle,
+    length, rotor cell index, stator cell index) for every piece of positive
+    length; with unequal partitions a cell may meet several pieces."""
     two_pi = 2.0 * np.pi
-    D = two_pi / n_R
-    rv = np.mod(theta + D * np.arange(n_R), two_pi)
-    sv = np.mod(D * np.arange(n_R), two_pi)
+    n_Rs = n_R if n_Rs is None else int(n_Rs)
+    Dr, Ds = two_pi / n_R, two_pi / n_Rs
+    rv = np.mod(theta + Dr * np.arange(n_R), two_pi)
+    sv = np.mod(Ds * np.arange(n_Rs), two_pi)
     cuts = np.sort(np.concatenate([rv, sv]))
     segs = []
     for i in range(len(cuts)):
@@ -36,8 +38,8 @@ def mortar_segments(theta, n_R):
         if L <= 1e-13:
             continue
         mid = a + 0.5 * L
-        jr = int(np.floor(np.mod(mid - theta, two_pi) / D)) % n_R
-        js = int(np.floor(np.mod(mid, two_pi) / D)) % n_R
+        jr = int(np.floor(np.mod(mid - theta, two_pi) / Dr)) % n_R
+        js = int(np.floor(np.mod(mid, two_pi) / Ds)) % n_Rs
         segs.append((a, L, jr, js))
     return segs
 
@@ -105,10 +107,12 @@ class Mortar:
         d = prob.d
         self.R = float(m.R)
         self.n_R = int(m.n_R)
+        self.n_Rs = int(getattr(m, "n_R_stator", 0) or self.n_R)     # stator partition (default: equal)
         self.n_z = int(m.n_z)
         D = 2.0 * np.pi / self.n_R
+        Ds = 2.0 * np.pi / self.n_Rs
         sg, wg = gauss_rule(prob.k + 1)
-        segs = mortar_segments(prob.theta, self.n_R)
+        segs = mortar_segments(prob.theta, self.n_R, self.n_Rs)
         phi0 = float(m.phi0)
         self.tau_cell = {}
         recs = []
@@ -118,7 +122,7 @@ class Mortar:
                 cs = int(m.iface_stator[lz, js])
                 rel = pa + sg * L
                 xr = face_coordinate(rel, prob.theta + jr * D, self.n_R)
-                xs = face_coordinate(rel, js * D, self.n_R)
+                xs = face_coordinate(rel, js * Ds, self.n_Rs)
                 phis = phi0 + rel
                 w = wg * self.R * L
                 if d == 2:

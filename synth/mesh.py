@@ -7,7 +7,9 @@ equally sized cells):
 * rotor disk r < R: an O-grid made of an m x m centre square (half width
   ``sq * R``) and four ring blocks of m x n_r cells blending the square's sides
   into the circle r = R; the interface therefore has n_R = 4 m cells;
-* stator annulus R < r < R_out: a polar grid of n_R x n_s cells;
+* stator annulus R < r < R_out: a polar grid of n_Rs x n_s cells, n_Rs = n_R
+  unless n_R_stator is given (unequal interface partitions, beyond the
+  paper's equal-partition restriction);
 * 3D: both are extruded along z in n_z layers over [0, H].
 
 Geometry nodes are the Q_k nodes of every cell (Gauss-Lobatto points in
@@ -61,13 +63,14 @@ class RotorStatorMesh:
     node_side: np.ndarray     # [N_n] uint8, 0 rotor, 1 stator
     wall: np.ndarray          # [N_n] uint8, 1 = stationary wall, 2 = wall moving with the rotor (blade)
     iface_rotor: np.ndarray   # [n_z, n_R] int32
-    iface_stator: np.ndarray  # [n_z, n_R] int32
+    iface_stator: np.ndarray  # [n_z, n_R_stator] int32
     R: float
     n_R: int
     n_z: int
     H: float
     phi0: float
     params: dict = field(default_factory=dict)
+    n_R_stator: int = 0       # stator interface cells per layer; 0: equal to n_R
 
     @property
     def n_nodes(self):
@@ -83,7 +86,7 @@ class RotorStatorMesh:
 
 
 def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55,
-                      phi0=-0.25 * np.pi, blades=0):
+                      phi0=-0.25 * np.pi, blades=0, n_R_stator=None):
     """Generate the merged rotor/stator mesh (see module docstring).
 
     blades > 0 (3D): that many radial blades inside the rotor, each the ring
@@ -96,7 +99,10 @@ def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55
     n = k + 1
     mk = m * k
     n_R = 4 * m
-    nRk = n_R * k
+    n_Rs = n_R if n_R_stator is None else int(n_R_stator)
+    if n_Rs < 1:
+        raise ValueError("n_R_stator >= 1 required")
+    nRk = n_Rs * k                                        # stator nodes per ring
     s = sq * R
 
     # ---- 2D rotor: centre square nodes
@@ -155,7 +161,7 @@ def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55
 
     # ---- 2D stator annulus
     rr = R + (R_out - R) * _param(n_s, k, g)
-    angp = _param(n_R, k, g)[:-1]                         # ia = 0..nRk-1
+    angp = _param(n_Rs, k, g)[:-1]                        # ia = 0..nRk-1
     phis = phi0 + 2.0 * np.pi * angp
     RR, PP = np.meshgrid(rr, phis, indexing="ij")         # [ir, ia]
     st_xy = np.stack([RR * np.cos(PP), RR * np.sin(PP)], axis=-1).reshape(-1, 2)
@@ -167,9 +173,9 @@ def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55
     def st_id(ir, ia_):
         return n_rot2 + ir * nRk + (ia_ % nRk)
 
-    st_cell_index = np.empty((n_R, n_s), dtype=np.int64)
+    st_cell_index = np.empty((n_Rs, n_s), dtype=np.int64)
     for jr in range(n_s):
-        for j in range(n_R):
+        for j in range(n_Rs):
             st_cell_index[j, jr] = len(cells2)
             cells2.append(st_id(jr * k + I0, j * k + I1))
     cells2 = np.asarray(cells2, dtype=np.int64)
@@ -183,13 +189,14 @@ def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55
     ifr2 = ring_cell_index[:, n_r - 1]
     ifs2 = st_cell_index[:, 0]
 
-    params = dict(d=d, k=k, m=m, n_r=n_r, n_s=n_s, n_z=n_z, R=R, R_out=R_out, H=H, sq=sq, phi0=phi0, blades=blades)
+    params = dict(d=d, k=k, m=m, n_r=n_r, n_s=n_s, n_z=n_z, R=R, R_out=R_out, H=H, sq=sq, phi0=phi0, blades=blades,
+                  n_R_stator=n_Rs)
     if d == 2:
         return RotorStatorMesh(d=2, k=k, x0=xy.copy(), cells=cells2.astype(np.int32),
                                cell_side=cell_side2, node_side=node_side2, wall=wall2,
                                iface_rotor=ifr2[None, :].astype(np.int32),
                                iface_stator=ifs2[None, :].astype(np.int32),
-                               R=R, n_R=n_R, n_z=1, H=1.0, phi0=phi0, params=params)
+                               R=R, n_R=n_R, n_z=1, H=1.0, phi0=phi0, params=params, n_R_stator=n_Rs)
 
     # ---- 3D extrusion: node id = iz * n2 + id2, cell id = lz * n_c2 + c2
     blade_cells2 = []
@@ -222,7 +229,7 @@ def rotor_stator_mesh(d, k, m, n_r, n_s, n_z=1, R=0.5, R_out=1.0, H=1.0, sq=0.55
     return RotorStatorMesh(d=3, k=k, x0=x3, cells=cells3.astype(np.int32), cell_side=cell_side3,
                            node_side=node_side3, wall=wall3, iface_rotor=ifr3.astype(np.int32),
                            iface_stator=ifs3.astype(np.int32), R=R, n_R=n_R, n_z=n_z, H=H,
-                           phi0=phi0, params=params)
+                           phi0=phi0, params=params, n_R_stator=n_Rs)
 
 
 def coarsen(params):
@@ -236,9 +243,13 @@ def coarsen(params):
     the fine cells subdivide the coarse cells in parameter space.
     """
     d, m, n_r, n_s, n_z = params["d"], params["m"], params["n_r"], params["n_s"], params["n_z"]
+    if params.get("n_R_stator") not in (None, 4 * m):
+        raise ValueError("coarsen: unequal interface partitions are not supported")
     if m % 2 or n_r % 2 or n_s % 2 or (d == 3 and n_z % 2):
         raise ValueError("m, n_r, n_s (and n_z in 3D) must be even to coarsen")
     cp = dict(params, m=m // 2, n_r=n_r // 2, n_s=n_s // 2, n_z=(n_z // 2 if d == 3 else n_z))
+    if "n_R_stator" in params:
+        cp["n_R_stator"] = 2 * m          # equal partitions on the coarse mesh too
     mc, n_R, n_Rc = m // 2, 4 * m, 2 * m
     parent, child = [], []
     # centre square (xi_0 = x, xi_1 = y), index cy*m + cx
