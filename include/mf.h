@@ -112,7 +112,12 @@ void mf_mesh_free(mf_mesh* m);
  * 0 < R < R_out, H > 0, 0 < sq < 1/sqrt 2, blades in 0..n_R and only in 3D) or
  * more than 2^31 - 1 nodes.
  * mf_mesh_params_defaults: d 3, k 2, m 8, n_r 2, n_s 4, n_z 8, R 0.5, R_out 1,
- * H 1, sq 0.55, phi0 -pi/4, no blades.
+ * H 1, sq 0.55, phi0 -pi/4, no blades, equal partitions.
+ * n_R_stator > 0 gives the stator its own number of interface cells per layer
+ * (unequal partitions, beyond the paper's equal-partition restriction); such
+ * meshes can be generated, read and coarsened-mapped only as equal ones can't
+ * (mf_mesh_coarsen_map rejects them), and mf_create rejects them with
+ * MF_ERR_ARG until the mortar kernels support them.
  * mf_mesh_sizes / mf_mesh_read: the mesh's sizes and a copy of its arrays into
  * caller HOST buffers sized as in mf_mesh_from_arrays (any pointer may be NULL).
  * mf_mesh_coarsen_map: the parameters of the uniformly coarsened mesh (every
@@ -128,9 +133,13 @@ typedef struct {
   double sq;
   double phi0;
   int    blades;
+  int    n_R_stator;   /* stator interface cells per layer; 0 = 4 m (equal partitions, the paper's case) */
 } mf_mesh_params;
 void mf_mesh_params_defaults(mf_mesh_params* p);
 mf_status mf_mesh_rotor_stator(const mf_mesh_params* p, mf_mesh** out);
+/* Interface partitions of a mesh: rotor and stator cells per z-layer, layers.
+ * iface_stator of mf_mesh_read holds n_z x n_R_stator entries. */
+mf_status mf_mesh_interface(const mf_mesh* m, int* n_R_rotor, int* n_R_stator, int* n_z);
 mf_status mf_mesh_sizes(const mf_mesh* m, int* d, int* k, int64_t* n_nodes, int64_t* n_cells, int* n_R, int* n_z);
 mf_status mf_mesh_read(const mf_mesh* m, double* x0, uint8_t* node_side, uint8_t* wall, int32_t* cells,
                        uint8_t* cell_side, int32_t* iface_rotor, int32_t* iface_stator);

@@ -94,18 +94,22 @@ def rotor_stator_mesh(**params):
         _check(lib.mf_mesh_sizes(mp, C.byref(d), C.byref(k), C.byref(nn), C.byref(nc), C.byref(n_R), C.byref(n_z)),
                None, "mf_mesh_sizes")
         d, k, nn, nc, n_R, n_z = d.value, k.value, nn.value, nc.value, n_R.value, n_z.value
+        nrs = C.c_int()
+        _check(lib.mf_mesh_interface(mp, None, C.byref(nrs), None), None, "mf_mesh_interface")
+        n_Rs = nrs.value
         x0 = np.empty((nn, d))
         ns, wall = np.empty(nn, np.uint8), np.empty(nn, np.uint8)
         cells = np.empty((nc, (k + 1) ** d), np.int32)
         cs = np.empty(nc, np.uint8)
-        ifr, ifs = np.empty((n_z, n_R), np.int32), np.empty((n_z, n_R), np.int32)
+        ifr, ifs = np.empty((n_z, n_R), np.int32), np.empty((n_z, n_Rs), np.int32)
         _check(lib.mf_mesh_read(mp, _np_ptr(x0), _np_ptr(ns), _np_ptr(wall), _np_ptr(cells), _np_ptr(cs),
                                 _np_ptr(ifr), _np_ptr(ifs)), None, "mf_mesh_read")
     finally:
         lib.mf_mesh_free(mp)
     pd = {f: getattr(p, f) for f, _ in _lib.MfMeshParams._fields_}
     return Mesh(d=d, k=k, x0=x0, cells=cells, cell_side=cs, node_side=ns, wall=wall, iface_rotor=ifr,
-                iface_stator=ifs, R=p.R, n_R=n_R, n_z=n_z, H=(p.H if d == 3 else 1.0), phi0=p.phi0, params=pd)
+                iface_stator=ifs, R=p.R, n_R=n_R, n_z=n_z, H=(p.H if d == 3 else 1.0), phi0=p.phi0, params=pd,
+                n_R_stator=n_Rs)
 
 
 def coarsen_map(**params):
@@ -126,6 +130,8 @@ def coarsen_map(**params):
 def _mesh_handle(mesh):
     """An mf_mesh (host copy) of a mesh object; free it with mf_mesh_free."""
     lib = _lib.load()
+    if getattr(mesh, "n_R_stator", 0) not in (0, int(mesh.n_R)):
+        raise MfError("unequal interface partitions: the operator supports equal rotor/stator partitions only")
     x0 = np.ascontiguousarray(mesh.x0, dtype=np.float64)
     ns = np.ascontiguousarray(mesh.node_side, dtype=np.uint8)
     wall = np.ascontiguousarray(mesh.wall, dtype=np.uint8)

@@ -16,7 +16,7 @@ MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG = 0, 1, 2, 3
 
 # every symbol include/mf.h declares
 EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_mesh_params_defaults", "mf_mesh_rotor_stator", "mf_mesh_sizes",
-           "mf_mesh_read", "mf_mesh_coarsen_map", "mf_checkpoint_write", "mf_checkpoint_read", "mf_log_open", "mf_create", "mf_destroy", "mf_last_error", "mf_sizes",
+           "mf_mesh_read", "mf_mesh_interface", "mf_mesh_coarsen_map", "mf_checkpoint_write", "mf_checkpoint_read", "mf_log_open", "mf_create", "mf_destroy", "mf_last_error", "mf_sizes",
            "mf_set_angle", "mf_node_coords", "mf_dirichlet", "mf_set_history", "mf_set_linearization",
            "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step",
            "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
@@ -29,7 +29,7 @@ PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "c
 class MfMeshParams(C.Structure):
     _fields_ = [("d", C.c_int), ("k", C.c_int), ("m", C.c_int), ("n_r", C.c_int), ("n_s", C.c_int),
                 ("n_z", C.c_int), ("R", C.c_double), ("R_out", C.c_double), ("H", C.c_double), ("sq", C.c_double),
-                ("phi0", C.c_double), ("blades", C.c_int)]
+                ("phi0", C.c_double), ("blades", C.c_int), ("n_R_stator", C.c_int)]
 
 
 class MfCheckpointInfo(C.Structure):
@@ -99,6 +99,7 @@ def load():
     lib.mf_mesh_sizes.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32),
                                   C.POINTER(i32)]
     lib.mf_mesh_read.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.mf_mesh_interface.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
     lib.mf_mesh_coarsen_map.argtypes = [C.POINTER(MfMeshParams), C.POINTER(MfMeshParams), vp, vp]
     lib.mf_log_open.argtypes = [C.c_char_p]
     lib.mf_checkpoint_write.argtypes = [C.c_char_p, vp, C.POINTER(MfCheckpointInfo), vp, vp]

@@ -30,6 +30,7 @@ struct mf_mesh {
   std::vector<int32_t> cells;
   double R, H, phi0;
   int n_R, n_z;
+  int n_Rs = 0;            // stator interface cells per layer (0: equal to n_R)
   std::vector<int32_t> ifr, ifs;
 };
 
@@ -378,6 +379,7 @@ static mf_status apply_angle(mf_ctx* h, double theta, cudaStream_t st) {
 extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega, double dt, int bdf,
                                const mf_options* opt, mf_handle* out) {
   if (!m || !out) return MF_ERR_ARG;
+  if (m->n_Rs != 0 && m->n_Rs != m->n_R) return MF_ERR_ARG;   // unequal partitions: no operator yet
   if (k != m->k || !(nu >= 0) || !std::isfinite(omega) || !(dt >= 0) || (bdf != 1 && bdf != 2)) return MF_ERR_ARG;
   mf_ctx* h = new mf_ctx();
   h->d = m->d; h->k = k; h->nn = m->nn; h->nc = m->nc; h->ndof = m->nn * (m->d + 1);

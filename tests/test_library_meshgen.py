@@ -86,3 +86,22 @@ def test_dof_per_cell_ratio_matches_the_papers_meshes():
         dofs = 4 * _node_count(3, c["k"], c["m"], c["n_r"], c["n_s"], c["n_z"])
         lo, hi = bands[c["k"]]
         assert lo <= dofs / cells <= hi, (name, cells, dofs, dofs / cells)
+
+
+@pytest.mark.parametrize("p", [dict(d=2, k=2, m=4, n_r=2, n_s=3, n_R_stator=12),
+                               dict(d=3, k=3, m=2, n_r=1, n_s=2, n_z=2, n_R_stator=11)],
+                         ids=["2d-12", "3d-11"])
+def test_generator_unequal_partitions_match_input_generator(p):
+    """Stator with its own number of interface cells: same arrays as the input
+    generator; the operator refuses such meshes (no mortar kernel for them yet)."""
+    from paper_2608_27423_b300 import rotor_stator_mesh, RotorStatorOperator, MfError
+    q = dict(p)
+    n_Rs = q.pop("n_R_stator")
+    ref = synth.rotor_stator_mesh(q["d"], q["k"], q["m"], q["n_r"], q["n_s"], q.get("n_z", 1), n_R_stator=n_Rs)
+    got = rotor_stator_mesh(**p)
+    assert got.n_R_stator == n_Rs and got.iface_stator.shape == ref.iface_stator.shape
+    for key in ("cells", "cell_side", "node_side", "wall", "iface_rotor", "iface_stator"):
+        assert np.array_equal(getattr(got, key), getattr(ref, key)), key
+    assert np.abs(got.x0 - ref.x0).max() < 1e-14
+    with pytest.raises(MfError):
+        RotorStatorOperator(got, 0.01, 1.0, 0.01, 1)
