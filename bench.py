@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--transient-rest", action="store_true",
                     help="start the transient from rest (u = 0; the blades and walls drive the flow)")
     ap.add_argument("--transient-no-eager", action="store_true", help="time only the graph-replayed steps")
+    ap.add_argument("--clocks-dir", default=None, help="where the nvidia-smi clock samples are written (default: temp)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default cells per block (profiling runs: timings under ncu are not representative)")
     return ap.parse_args()
@@ -614,8 +615,9 @@ def main():
         return e0.elapsed_time(e1)
 
     # ---- FP64 apply: the headline
-    sampler = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    import tempfile
+    clocks_dir = args.clocks_dir or tempfile.gettempdir()
+    sampler = ClockSampler(os.path.join(clocks_dir, f"clocks_rank{rank}.csv"))
     for _ in range(args.warmup):
         op.apply_jacobian(x, y)
     torch.cuda.synchronize()

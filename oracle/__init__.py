@@ -22,10 +22,15 @@ Pieces (each function names the passage it follows):
 * ``solve``   -- Dirichlet constraints, restarted GMRES / dense solves, Newton
                  (Eq. Eq-Newton-method).
 
-Readings of passages that are silent or garbled are listed in the design doc of the
-repository (S1..S21) and are the same ones the CUDA library takes.  Parity
-status: every operator term is pinned by a test that does not re-derive it
-(null space, conforming identity, assembled vs matrix-free, finite-difference
-Jacobian, SIPG Stokes definiteness, quadrature invariants, manufactured-solution
-convergence rates).
+Where the paper is silent or garbled, this package takes the same readings as
+the CUDA library: the jump is own minus other with the own outward normal, the
+face penalty is the larger of the two cells' values with F = 1, every
+non-interface face enters the penalty with weight 1/2, h is the diameter of
+the equal-volume circle (2D) or sphere (3D), k+1 Gauss points per direction,
+Gauss-Lobatto nodes, mortar points on the exact circle with weights w R dphi
+(dz), tau frozen in the Jacobian, no convective flux across the interface.
+Parity status: every operator term is pinned by a test that does not re-derive
+it (null space, conforming identity, assembled vs matrix-free, finite-difference
+Jacobian, SIPG Stokes definiteness, quadrature invariants, rotation symmetry,
+manufactured-solution convergence rates in 2D and 3D, a Taylor-Green step).
 """
