@@ -140,6 +140,18 @@ mf_status mf_mesh_rotor_stator(const mf_mesh_params* p, mf_mesh** out);
 /* Interface partitions of a mesh: rotor and stator cells per z-layer, layers.
  * iface_stator of mf_mesh_read holds n_z x n_R_stator entries. */
 mf_status mf_mesh_interface(const mf_mesh* m, int* n_R_rotor, int* n_R_stator, int* n_z);
+
+/* mf_mortar_segments: the mortar segments of an interface whose rotor has n_R
+ * and whose stator has n_Rs equal cells (Section 3.2; the paper's case is
+ * n_Rs = n_R): the circle is cut at every rotor vertex theta + 2 pi i / n_R
+ * and every stator vertex 2 pi j / n_Rs (angles from the partitions' common
+ * origin); each piece longer than 1e-13 is a segment with its start angle in
+ * [0, 2 pi), its length, and the rotor and stator cells it lies in.  HOST
+ * arrays of max_out entries (any may be NULL); *count receives the number of
+ * segments (at most n_R + n_Rs).  MF_ERR_ARG for bad sizes, a non-finite
+ * angle, or max_out < *count (nothing beyond max_out is written).  Host code. */
+mf_status mf_mortar_segments(int n_R, int n_Rs, double theta, int max_out, double* start, double* length,
+                             int32_t* rotor_cell, int32_t* stator_cell, int* count);
 mf_status mf_mesh_sizes(const mf_mesh* m, int* d, int* k, int64_t* n_nodes, int64_t* n_cells, int* n_R, int* n_z);
 mf_status mf_mesh_read(const mf_mesh* m, double* x0, uint8_t* node_side, uint8_t* wall, int32_t* cells,
                        uint8_t* cell_side, int32_t* iface_rotor, int32_t* iface_stator);

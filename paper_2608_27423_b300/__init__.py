@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import MF_FP64, MF_FP32, MF_DF64, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
     MfSolverOpts, MfSolveReport
 
-__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "log_open", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
+__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "log_open", "mortar_segments", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
            "solver_defaults"]
 
 
@@ -110,6 +110,21 @@ def rotor_stator_mesh(**params):
     return Mesh(d=d, k=k, x0=x0, cells=cells, cell_side=cs, node_side=ns, wall=wall, iface_rotor=ifr,
                 iface_stator=ifs, R=p.R, n_R=n_R, n_z=n_z, H=(p.H if d == 3 else 1.0), phi0=p.phi0, params=pd,
                 n_R_stator=n_Rs)
+
+
+def mortar_segments(n_R, n_Rs, theta):
+    """Mortar segments of an interface with n_R rotor and n_Rs stator cells at
+    rotor angle theta (mf_mortar_segments): arrays start, length, rotor cell,
+    stator cell."""
+    lib = _lib.load()
+    cap = int(n_R) + int(n_Rs)
+    a, L = np.empty(cap), np.empty(cap)
+    jr, js = np.empty(cap, np.int32), np.empty(cap, np.int32)
+    cnt = C.c_int()
+    _check(lib.mf_mortar_segments(int(n_R), int(n_Rs), float(theta), cap, _np_ptr(a), _np_ptr(L), _np_ptr(jr),
+                                  _np_ptr(js), C.byref(cnt)), None, "mf_mortar_segments")
+    c = cnt.value
+    return a[:c], L[:c], jr[:c], js[:c]
 
 
 def coarsen_map(**params):

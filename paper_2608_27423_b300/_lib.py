@@ -16,7 +16,7 @@ MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG = 0, 1, 2, 3
 
 # every symbol include/mf.h declares
 EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_mesh_params_defaults", "mf_mesh_rotor_stator", "mf_mesh_sizes",
-           "mf_mesh_read", "mf_mesh_interface", "mf_mesh_coarsen_map", "mf_checkpoint_write", "mf_checkpoint_read", "mf_log_open", "mf_create", "mf_destroy", "mf_last_error", "mf_sizes",
+           "mf_mesh_read", "mf_mesh_interface", "mf_mortar_segments", "mf_mesh_coarsen_map", "mf_checkpoint_write", "mf_checkpoint_read", "mf_log_open", "mf_create", "mf_destroy", "mf_last_error", "mf_sizes",
            "mf_set_angle", "mf_node_coords", "mf_dirichlet", "mf_set_history", "mf_set_linearization",
            "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step",
            "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
@@ -100,6 +100,7 @@ def load():
                                   C.POINTER(i32)]
     lib.mf_mesh_read.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.mf_mesh_interface.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+    lib.mf_mortar_segments.argtypes = [i32, i32, dbl, i32, vp, vp, vp, vp, C.POINTER(i32)]
     lib.mf_mesh_coarsen_map.argtypes = [C.POINTER(MfMeshParams), C.POINTER(MfMeshParams), vp, vp]
     lib.mf_log_open.argtypes = [C.c_char_p]
     lib.mf_checkpoint_write.argtypes = [C.c_char_p, vp, C.POINTER(MfCheckpointInfo), vp, vp]

@@ -97,3 +97,18 @@ def test_unequal_mms_converges_like_equal_partitions():
     e_eq = [err(m, 4 * m) for m in (8, 16)]
     r_un, r_eq = np.log2(e_un[0] / e_un[1]), np.log2(e_eq[0] / e_eq[1])
     assert r_un > 2 + 1 - 0.35 and abs(r_un - r_eq) < 0.3, (e_un, e_eq)
+
+
+@pytest.mark.parametrize("n_R,n_Rs", [(16, 16), (16, 12), (16, 20), (8, 7), (64, 48)])
+def test_library_segments_equal_the_oracles(n_R, n_Rs):
+    """The library's host-side segment builder (mf_mortar_segments) gives the
+    oracle's segments: same pieces, cells and lengths (to roundoff)."""
+    from paper_2608_27423_b300 import mortar_segments as lib_segments
+    rng = np.random.default_rng(n_R * 100 + n_Rs)
+    for theta in [0.0, 1e-12, 2 * np.pi / n_R * 3, -0.4, 7.3] + list(rng.uniform(-10, 10, 5)):
+        ref = mortar_segments(theta, n_R, n_Rs)
+        a, L, jr, js = lib_segments(n_R, n_Rs, theta)
+        assert len(ref) == len(a), (theta, len(ref), len(a))
+        for (ra, rL, rjr, rjs), x, y, p, q in zip(ref, a, L, jr, js):
+            assert (rjr, rjs) == (p, q) and abs(rL - y) < 1e-13 and abs(np.mod(ra - x + 1, 2 * np.pi) - 1) < 1e-13
+        assert abs(L.sum() - 2 * np.pi) < 1e-12
