@@ -71,6 +71,7 @@ struct Workspace {
   float* f_Vin = nullptr;    // [(mi+1) n] inner FP32 Krylov basis
   double* c_Vin = nullptr;   // [(mi+1) n] inner FP64 Krylov basis
   double* hin = nullptr;     // device inner Hessenberg columns
+  bool is_static = false;    // a view into mf_solve_step_static's device array: never allocated, grown or freed
 };
 
 struct mf_ctx;
@@ -331,6 +332,7 @@ extern "C" void mf_mesh_free(mf_mesh* m) { delete m; }
 
 // ------------------------------------------------------------------ create
 static void free_ws(Workspace& w) {
+  if (w.is_static) { w = Workspace(); return; }   // symbol memory: nothing to free
   void* ptrs[] = {w.V, w.Z, w.w, w.r, w.dx, w.hcol, w.part, w.diag64, w.dinv64, w.dinv32, w.f_v, w.f_x, w.f_r,
                   w.f_d, w.f_t, w.f_w, w.c_x, w.c_r, w.c_d, w.c_t, w.c_v, w.c_w, w.utrial, w.f_Vin, w.c_Vin, w.hin, w.ep, w.jep,
                   w.hout, w.rec, w.rec_count};
@@ -393,7 +395,7 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
   h->nm = (int64_t)m->n_z * m->n_R * 2;
   h->nif = (int64_t)m->n_z * m->n_R;
   h->ncache = (m->d == 2) ? Cache<2>::NF : Cache<3>::NF;
-  h->nb = 148 * 4;
+  h->nb = MF_REDUCE_BLOCKS;
   mf_status s = upload_tables(h);
   if (s != MF_OK) { mf_destroy(h); return s; }
   const int npc = ipow(k + 1, m->d);
@@ -647,6 +649,7 @@ extern "C" mf_status mf_profile_read(mf_handle h, mf_profile_t* out) {
 #include "mf_mg.inc"
 #include "mf_transient.inc"
 #include "mf_autotune.inc"
+#include "mf_probe.inc"
 
 // ---------------------------------------------------------------- batched instances
 struct mf_batch {
@@ -904,6 +907,13 @@ extern "C" mf_status mf_solve_step_static(mf_handle h, double* up, const mf_solv
   view.part = p; p += (size_t)part_cap * h->nb;
   view.part_cap = part_cap;
   view.pinned = g_static_host;
+  // The Jacobi / FP64 Newton-FGMRES path reads and writes only the fields set
+  // above (V, Z, w, r, dx, diag64, dinv64, dinv32, utrial, ep, jep, hcol, part,
+  // pinned).  The FP32 / Chebyshev vectors, the inner GMRES bases and the
+  // transient buffers stay null; a solver path that asks for them (or for a
+  // larger workspace) gets MF_ERR_STATE from ensure_ws / ensure_inner instead of
+  // an allocation, because the view is marked static.
+  view.is_static = true;
   // the small scalars start at zero on every call
   CK(cudaMemsetAsync(view.hcol, 0, sizeof(double) * (3 * (m + 2) + (size_t)part_cap * h->nb), S(stream)));
   Workspace saved = h->ws;

@@ -75,11 +75,11 @@ def test_fullsize_sampled_rows(name):
     yr = _rows_oracle(mesh, prm, f, nodes, f["up_star"], "res")
     y = y.cpu().numpy()[nodes]
     ydf = ydf.cpu().numpy()[nodes]
-    assert np.linalg.norm(ydf - yj) <= 1e-12 * np.linalg.norm(yj)
     y32 = y32.double().cpu().numpy()[nodes]
     r = r.cpu().numpy()[nodes]
-    assert np.linalg.norm(y - yj) <= 1e-12 * np.linalg.norm(yj)
-    assert np.linalg.norm(y32 - yj) <= 1e-5 * np.linalg.norm(yj)
-    assert np.linalg.norm(r - yr) <= 1e-12 * np.linalg.norm(yr)
+    # normwise and element-wise (max-entry error / max entry) on the sampled rows
+    for got, ref, tol in ((ydf, yj, 1e-12), (y, yj, 1e-12), (y32, yj, 1e-5), (r, yr, 1e-12)):
+        assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
     # properties at any size: finite everywhere, wall rows copied
     assert np.isfinite(y).all()

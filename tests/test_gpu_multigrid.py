@@ -117,3 +117,49 @@ def test_multigrid_preconditioned_newton_matches_oracle():
     assert st == 0, (st, g.last_error(), list(rep.res_norm[:rep.newton_iters + 1]))
     du, dp = _compare(up.cpu().numpy(), ref)
     assert du < 1e-8 and dp < 1e-6, (du, dp)
+
+
+@pytest.fixture(scope="module")
+def q3_case():
+    """3D Q3 cylinder (72 hexes, 10,108 DoFs), BDF2, and the oracle's direct
+    Newton solution of its step (computed once for both precisions)."""
+    from tests.test_gpu_solver import _oracle_solution
+    prm = dict(nu=0.05, omega=1.0, dt=0.01, bdf=2, theta=0.137)
+    cfg = dict(d=3, k=3, m=2, n_r=2, n_s=2, n_z=2)
+    mesh, _, f = synth.make_config(**cfg, seed=23, **prm)
+    u0 = np.zeros((mesh.n_nodes, 4))
+    u0[:, :3] = f["u_n"]
+    u0[mesh.wall.astype(bool), :3] = 0.0
+    f = dict(f, u_n_full=u0)
+    ref, red = _oracle_solution(mesh, prm, f)
+    assert red < 1e-12
+    return cfg, prm, mesh, f, ref
+
+
+@pytest.mark.parametrize("pc_prec", ["fp32", "fp64"])
+def test_polynomial_multigrid_q3_newton_matches_oracle(q3_case, pc_prec):
+    """The polynomial level of the mixed solve (Q3 -> Q2 on the same cells) and
+    one geometric level below it (Q2, every block halved): FGMRES in FP64
+    preconditioned by the V-cycle with FP32 (mixed) or FP64 operator applies.
+    The Newton solution equals the oracle's direct Newton solution (sparse LU
+    of the assembled Jacobian at every step)."""
+    from paper_2608_27423_b300 import RotorStatorOperator, solver_defaults, MF_PC_MG, MF_FP32, MF_FP64
+    from tests.test_gpu_solver import _compare
+    cfg, prm, mesh, f, ref = q3_case
+    pmesh = synth.rotor_stator_mesh(3, 2, cfg["m"], cfg["n_r"], cfg["n_s"], cfg["n_z"])
+    cp, parent, child = coarsen(dict(cfg, k=2))
+    cmesh = synth.rotor_stator_mesh(3, 2, cp["m"], cp["n_r"], cp["n_s"], cp["n_z"])
+    ops = [RotorStatorOperator(mm, prm["nu"], prm["omega"], prm["dt"], prm["bdf"]) for mm in (mesh, pmesh, cmesh)]
+    ops[0].mg_attach(ops[1])                      # polynomial: Q3 -> Q2, same cells
+    ops[1].mg_attach(ops[2], parent, child)       # geometric: Q2 -> Q2 on the halved mesh
+    g = ops[0]
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    g.set_history(T(f["u_n"]), T(f["u_nm1"]))
+    up = T(f["u_n_full"])
+    st, rep = g.solve_step(up, solver_defaults(theta=prm["theta"], pc=MF_PC_MG,
+                                               pc_precision=MF_FP32 if pc_prec == "fp32" else MF_FP64,
+                                               newton_rtol=1e-11, lin_rtol=1e-6, max_newton=40, restart=30,
+                                               max_lin_iters=300, mg_smooth=3, mg_coarse_iters=30))
+    assert st == 0, (st, g.last_error(), list(rep.res_norm[:rep.newton_iters + 1]))
+    du, dp = _compare(up.cpu().numpy(), ref)
+    assert du < 1e-8 and dp < 1e-6, (du, dp)

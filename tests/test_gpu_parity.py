@@ -1,7 +1,9 @@
 """GPU parity: the CUDA library against the CPU FP64 oracle on the same seeded inputs.
 
-Bars (normwise, ||y_gpu - y_oracle||_2 / ||y_oracle||_2): 1e-12 for FP64 applies,
-residuals and diagonals; 1e-5 for FP32 applies.
+Bars, both checked: normwise ||y_gpu - y_oracle||_2 / ||y_oracle||_2 and
+element-wise max_i |y_gpu,i - y_oracle,i| / ||y_oracle||_inf (a localised error
+on the few interface rows is not diluted by the interior rows); 1e-12 for FP64
+applies, residuals and diagonals; 1e-5 for FP32 applies.
 """
 import numpy as np
 import pytest
@@ -17,7 +19,11 @@ TOL32 = 1e-5
 
 
 def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    """max(normwise relative error, max-entry error / ||b||_inf)."""
+    a, b = np.asarray(a), np.asarray(b)
+    nw = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    ew = float(np.abs(a - b).max() / np.abs(b).max())
+    return max(nw, ew)
 
 
 def setup(d, k, m, n_r, n_s, n_z=1, bdf=2, theta=0.137, nu=0.05, omega=1.0, dt=0.01, state="iid", seed=11, blades=0):
@@ -68,7 +74,7 @@ def test_residual_matches_oracle(c):
     assert rel(r.cpu().numpy(), r_ref) <= TOL64
 
 
-@pytest.mark.parametrize("c", CASES[:5], ids=cid)
+@pytest.mark.parametrize("c", CASES, ids=cid)
 def test_jacobian_fp32_matches_oracle(c):
     mesh, prm, f, op, g, T = setup(**c)
     y_ref = op.apply(f["x"])
@@ -90,7 +96,7 @@ def test_jacobian_df64_matches_oracle_at_fp64_bar(c):
     assert rel(y.cpu().numpy(), y_ref) <= TOL64
 
 
-@pytest.mark.parametrize("c", CASES[:5], ids=cid)
+@pytest.mark.parametrize("c", CASES, ids=cid)
 def test_diagonal_matches_assembled(c):
     mesh, prm, f, op, g, T = setup(**c)
     dref = op.diagonal()

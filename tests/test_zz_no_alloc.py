@@ -63,6 +63,34 @@ def test_static_workspace_solve_matches_allocating_solve():
         assert abs(rep2.newton_iters - rep.newton_iters) <= 1
 
 
+def test_static_workspace_call_allocates_no_device_memory():
+    """On a freshly created handle that never ran mf_solve_step, two static
+    calls in a row leave the device's free memory unchanged (cudaMemGetInfo
+    through torch.cuda.mem_get_info, after a synchronize).  A warm-up call on
+    another handle first loads every kernel the solve launches, so lazy module
+    loading does not show up as an allocation."""
+    from paper_2608_27423_b300 import _lib, MfSolveReport
+    lib = _lib.load()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _, prm, warm, u_w = _problem()
+    o = _opts(prm["theta"])
+    rep = MfSolveReport()
+    assert lib.mf_solve_step_static(warm.h, C.c_void_p(u_w.data_ptr()), C.byref(o), C.byref(rep), stream) == 0
+    _, prm, fresh, u0 = _problem()
+    ups = [u0.clone(), u0.clone()]
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for up in ups:
+        st = lib.mf_solve_step_static(fresh.h, C.c_void_p(up.data_ptr()), C.byref(o), C.byref(rep), stream)
+        assert st == 0, fresh.last_error()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    # the fresh handle's result equals the warm handle's (same problem)
+    du, dp = _rel(ups[1], u_w)
+    assert du < 1e-8 and dp < 1e-6, (du, dp)
+
+
 def test_static_workspace_rejects_oversized_problems():
     from paper_2608_27423_b300 import _lib, MfSolveReport, MF_PC_GMRES, RotorStatorOperator
     lib = _lib.load()
