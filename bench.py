@@ -29,7 +29,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Jacobian-apply DoFs/s (FP64 vs FP32) at Q2/Q3; time to 1e-8 residual per step"
 FP64_NOMINAL_TFLOPS = 1.25       # B300 FP64 (non-tensor) nominal
-FP64_PROBE_TFLOPS = 1.128        # FMA-chain probe on the B300s
 # DRAM bytes (read + write) per cell of k_cell_jac<3,2,double,9> from one ncu capture on the 16,384-hex
 # cylinder (profiles/k_cell_jac_fp64_3d_q2_mid.md: 134.740 MB + 4.888 MB); traffic scales with the cells.
 TRAFFIC_BYTES_PER_CELL_Q2_3D_FP64 = (134.739968e6 + 4.887808e6) / 16384
@@ -55,6 +54,8 @@ def parse():
                     help="start the transient from rest (u = 0; the blades and walls drive the flow)")
     ap.add_argument("--transient-no-eager", action="store_true", help="time only the graph-replayed steps")
     ap.add_argument("--clocks-dir", default=None, help="where the nvidia-smi clock samples are written (default: temp)")
+    ap.add_argument("--q3-workload", default="3d_q3", help="the Q3 workload of the q3 leg")
+    ap.add_argument("--no-q3", action="store_true", help="skip the Q3 leg")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default cells per block (profiling runs: timings under ncu are not representative)")
     return ap.parse_args()
@@ -178,7 +179,7 @@ def build_levels(op, cfg, prm, n_h):
     return levels
 
 
-def solve_leg(args, op, mesh, prm, f, T):
+def solve_leg(args, op, mesh, prm, f, T, workload=None):
     """Newton + FGMRES(30) (FP64 residual, Jacobian applies and CGS2)
     preconditioned by one V-cycle of the global-coarsening multigrid (GMRES-Jacobi
     smoothing), with the V-cycle's operator applies in FP32 (mixed) or FP64.
@@ -187,7 +188,7 @@ def solve_leg(args, op, mesh, prm, f, T):
     from paper_2608_27423_b300 import MF_PC_MG, MF_FP32, MF_FP64, solver_defaults
     from synth.configs import CONFIGS
     d = mesh.d
-    cfg = CONFIGS[args.workload]
+    cfg = CONFIGS[workload or args.workload]
     levels = build_levels(op, cfg, prm, args.mg_levels - 1)
     u0 = np.zeros_like(f["up_star"])
     u0[:, :d] = f["u_n"]
@@ -357,6 +358,67 @@ def batched_leg(args, T, dev):
     out["solve_rel_diff_batched_vs_one_by_one"] = [float((a[:, :3] - b[:, :3]).norm() / b[:, :3].norm())
                                                    for a, b in zip(sols["batched"], sols["one_by_one"])]
     return out
+
+
+# --------------------------------------------------------------------- Q3 leg
+def q3_leg(args, T, timed):
+    """The Q3 cylinder (59,904 Q3 hexes, 6,685,924 DoFs, Re = 200, BDF2): FP64,
+    FP32 and double-float Jacobian-apply DoFs/s with the autotuned launch
+    shape, and (unless --no-solve) the Newton step to 1e-8 with the FP32
+    p-multigrid (Q3 -> Q2 -> geometric Q2 levels) against the all-FP64
+    multigrid, with the relative solution difference."""
+    import torch
+    from paper_2608_27423_b300 import RotorStatorOperator, MF_FP32, MF_DF64
+    name = args.q3_workload
+    mesh, prm, f = build_inputs(name)
+    op = RotorStatorOperator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
+    up_star = T(f["up_star"])
+    op.set_history(T(f["u_n"]), T(f["u_nm1"]))
+    op.set_linearization(up_star, prm["theta"])
+    out = {"workload": name, "n_cells": op.n_cells, "n_dofs": op.n_dofs, "k": mesh.k}
+    if not args.no_autotune:
+        tune = op.autotune()
+        out["cells_per_block"] = {p: tune[p]["chosen"] for p in ("fp64", "fp32")}
+    x = T(f["x"])
+    y = torch.empty_like(x)
+    steps = max(20, args.steps // 3)
+    op.profile(True)
+    ms = timed(lambda: op.apply_jacobian(x, y), steps, 3)
+    prof = op.profile_read()
+    op.profile(False)
+    nl, kms = prof["cell_jac_fp64"]
+    out["fp64_apply_dofs_per_s"] = op.n_dofs / (ms / steps * 1e-3)
+    out["fp64_cell_kernel_ms"] = kms / max(nl, 1)
+    out["fp64_cell_kernel_tflops"] = algorithmic_flops_per_cell(mesh.d, mesh.k) * op.n_cells / (
+        out["fp64_cell_kernel_ms"] * 1e-3) / 1e12
+    x32 = x.float()
+    y32 = torch.empty_like(x32)
+    ms32 = timed(lambda: op.apply_jacobian(x32, y32, prec=MF_FP32), steps, 3)
+    out["fp32_apply_dofs_per_s"] = op.n_dofs / (ms32 / steps * 1e-3)
+    ydf = torch.empty_like(x)
+    msdf = timed(lambda: op.apply_jacobian(x, ydf, prec=MF_DF64), steps, 3)
+    out["df64_apply_dofs_per_s"] = op.n_dofs / (msdf / steps * 1e-3)
+    out["df64_vs_fp64_rel_diff"] = float((ydf - y).norm() / y.norm())
+    out["fp32_vs_fp64_rel_diff"] = float((y32.double() - y).norm() / y.norm())
+    if not args.no_solve:
+        out["solve_to_1e-8"] = solve_leg(args, op, mesh, prm, f, T, workload=name)
+    return out
+
+
+def peaks_leg(clocks_path, local):
+    """Measured FMA rates of this GPU (mf_fma_peak: a hand-written kernel of
+    independent FMA chains on every SM, CUDA events) in FP64 and FP32, with the
+    SM clock sampled while they run."""
+    from paper_2608_27423_b300 import fma_peak, MF_FP64, MF_FP32
+    sampler = ClockSampler(clocks_path)
+    sampler.start()
+    f64, ms64 = fma_peak(MF_FP64)
+    f32, ms32 = fma_peak(MF_FP32)
+    clocks = sampler.stop(local)
+    return {"fp64_tflops": f64, "fp32_tflops": f32, "fp64_probe_ms": ms64, "fp32_probe_ms": ms32,
+            "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS, "clocks": clocks,
+            "how": "mf_fma_peak: 8 independent FMA chains per thread, 2048 threads per SM on every SM, "
+                   "2 warm-up + 5 timed launches (CUDA events)"}
 
 
 # --------------------------------------------------------------------- CPU oracle
@@ -631,6 +693,15 @@ def main():
     ms_step = t_max / args.steps
     value = dofs_all / (ms_step * 1e-3)
 
+    # measured FMA peaks of this GPU (the ALU roofline's denominators)
+    try:
+        peaks = peaks_leg(os.path.join(clocks_dir, f"clocks_peaks_rank{rank}.csv"), local)
+    except Exception as exc:
+        peaks = {"error": repr(exc)}
+    fp64_peak = peaks.get("fp64_tflops") or FP64_NOMINAL_TFLOPS
+    peak_source = ("measured in this run: mf_fma_peak FP64 FMA chains (nominal 1.25 TFLOP/s beside it)"
+                   if peaks.get("fp64_tflops") else "recipe nominal FP64 1.25 TFLOP/s (probe failed)")
+
     # dominant kernel roofline (FP64 cell Jacobian, bound by the FP64 pipe)
     nl, kms = prof["cell_jac_fp64"]
     k_ms = kms / max(nl, 1)
@@ -640,10 +711,11 @@ def main():
     achieved_tf = flops / (k_ms * 1e-3) / 1e12
     traffic = (TRAFFIC_BYTES_PER_CELL_Q2_3D_FP64 * op.n_cells
                if (d, k) == (3, 2) and tune["fp64"]["chosen"] == 9 else None)
-    roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(achieved_tf / FP64_NOMINAL_TFLOPS, 4), "traffic": traffic,
+    roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(fp64_peak, 4),
+                "unit": "TFLOP/s", "frac": round(achieved_tf / fp64_peak, 4), "traffic": traffic,
                 "kernel": f"k_cell_jac<{d},{k},double,{tune['fp64']['chosen']}>", "kernel_ms": round(k_ms, 4),
-                "flops_per_launch": flops, "peak_source": "recipe nominal FP64 1.25 TFLOP/s (probe 1.128)",
+                "flops_per_launch": flops, "peak_source": peak_source,
+                "frac_of_nominal": round(achieved_tf / FP64_NOMINAL_TFLOPS, 4),
                 "hbm": {"achieved_gbs": round(byts / (k_ms * 1e-3) / 1e9, 1),
                         "algorithmic_bytes": byts}}
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -653,7 +725,7 @@ def main():
         roofline["hbm"]["frac"] = round(roofline["hbm"]["achieved_gbs"] / pk["hbm_gbs"], 4)
     shares = {kk: {"launches": v[0], "ms": round(v[1], 3)} for kk, v in prof.items() if v[0]}
 
-    extra = {"autotune": tune}
+    extra = {"autotune": tune, "peaks": peaks}
     # ---- FP32 apply
     x32 = x.float()
     y32 = torch.empty_like(x32)
@@ -699,6 +771,8 @@ def main():
     if not args.no_solve:
         leg("solve_to_1e-8", lambda: solve_leg(args, op, mesh, prm, f, T))
         op.set_linearization(up_star, prm["theta"])
+    if not args.no_q3:
+        leg("q3", lambda: q3_leg(args, T, timed))
     if args.batched:
         leg("batched_12", lambda: batched_leg(args, T, dev))
     if args.transient > 0:

@@ -26,8 +26,13 @@
  *     those documented as synchronising.
  *   - Velocity components on wall nodes carry homogeneous (or mf_dirichlet)
  *     Dirichlet conditions: Jacobian rows/columns there are identity and the
- *     residual there is u - g.  Pressure is unconstrained (the constant
- *     pressure is a near null vector; solves remove the pressure mean).
+ *     residual there is u - g.  Pressure is unconstrained.  The constant
+ *     pressure is only a near null vector of the discrete operator (the mortar
+ *     integrates the exact circle while a cell's divergence theorem uses its
+ *     polynomial face, an O(h^k) defect on interface rows), so the equations
+ *     fix the pressure level weakly and no solve removes a pressure mean;
+ *     mf_solver_opts.deflate_pressure optionally minimises the residual along
+ *     J e_p at each FGMRES restart (off by default).
  *   - Every call returns an mf_status; on failure mf_last_error(h) holds a
  *     message.  No call throws across the ABI.
  */
@@ -202,6 +207,11 @@ typedef struct {
 } mf_options;
 
 /* mf_create: set up the operator on the current CUDA device (synchronising).
+ * Parameters of the ALE Navier-Stokes problem of Eq. EqNS (nu, the rotor's
+ * omega) and of its discretisation: Q_k shape functions (Eq.
+ * Eq-shape-functions), the time step that enters tau (Eq. Eq-stab-param) and
+ * the BDF order of the time integration (Section 4: BDF2 in the transient
+ * examples), the penalty factor F of Eq. EqPenalty in opt.
  *   k must equal the mesh degree; nu >= 0 kinematic viscosity; omega rotor
  *   angular velocity about e_z; dt > 0 time step of BDF order bdf (1|2), or
  *   dt = 0 for the steady operator (time terms and the (1/dt)^2 part of tau
@@ -227,11 +237,15 @@ mf_status mf_node_coords(mf_handle h, double* xyz_out, void* stream);
  * the rigid rotation omega e_z x x of the current angle instead. */
 mf_status mf_dirichlet(mf_handle h, const double* g, void* stream);
 
-/* BDF history (device [n_nodes][d] each; u_nm1 ignored/NULL for BDF1):
- * stores h_t = (alpha_1 u^n + alpha_2 u^{n-1}) / dt. */
+/* BDF history (Section 4: backward-difference time integration of the time
+ * derivative of Eq. EqNS; device [n_nodes][d] each; u_nm1 ignored/NULL for
+ * BDF1): stores h_t = (alpha_1 u^n + alpha_2 u^{n-1}) / dt with alpha =
+ * (1, -1) for BDF1 and (3/2, -2, 1/2) for BDF2 at constant dt. */
 mf_status mf_set_history(mf_handle h, const double* u_n, const double* u_nm1, void* stream);
 
-/* Linearisation state (device [n_nodes][d+1] FP64) at rotor angle theta:
+/* Linearisation state u*, p* of the Newton Jacobian (Section 2.3 blocks
+ * A-hat..D-hat) at rotor angle theta (rotation, Section 3.1; mortar cells and
+ * points, Section 3.2).  up_star: device [n_nodes][d+1] FP64.  The call
  * rotates, remaps the mortar, and caches per Gauss point the geometry and the
  * frozen-tau linearisation (advection u*-u_ALE, grad u*, strong residual R*,
  * tau) in FP64 and an FP32 copy.  Must precede mf_apply_jacobian/mf_diagonal. */
@@ -241,7 +255,10 @@ mf_status mf_set_linearization(mf_handle h, const double* up_star, double theta,
  * velocity DoFs.  up, r: device [n_nodes][d+1] FP64; tau from up itself. */
 mf_status mf_residual(mf_handle h, const double* up, double* r, void* stream);
 
-/* y = J x at the current linearisation.  prec MF_FP64: x, y double; MF_FP32:
+/* y = J x at the current linearisation: the Jacobian of the residual of Eq.
+ * Eq-NSweakWmortar with the SUPG/PSPG terms of Eq. Eq-NSweakComplete, i.e.
+ * the blocks A-hat..D-hat of Section 2.3 (tau frozen) plus the mortar face
+ * terms of Eqs. EqMortarPre, EqMortarDiff, EqMortarMass.  prec MF_FP64: x, y double; MF_FP32:
  * x, y float (FP32 cache); MF_DF64: x, y double, double-float arithmetic (its
  * cache copy is built on the first such call after each linearisation).  x entries on wall velocity DoFs are ignored as
  * inputs and copied to y (identity rows/columns).  x and y must not alias. */
@@ -299,7 +316,8 @@ typedef struct {
 
 void mf_solver_defaults(mf_solver_opts* o);
 
-/* One nonlinear step: Newton on R(up) = 0 at angle so->theta, each linear
+/* One nonlinear step: Newton on R(up) = 0 (Eq. Eq-Newton-method: solve
+ * J [du, dp] = -R, update, repeat) at angle so->theta, each linear
  * system by right-preconditioned FGMRES with FP64 residual, Jacobian applies
  * and CGS2 orthogonalisation.  up: device [n_nodes][d+1] FP64, in: initial
  * guess, out: solution.  Synchronising (reads convergence data back);
@@ -389,9 +407,11 @@ mf_status mf_run_transient(mf_handle h, double* u_n, double* u_nm1, int n_steps,
  * holds until the process exits.  The call allocates no device or pinned host
  * memory: no cudaMalloc, cudaFree, cudaMallocHost or event creation.  Limits:
  *   - pc must be MF_PC_JACOBI with pc_precision MF_FP64 and outer_precision MF_FP64;
- *   - (2*restart + 10) * n_dofs + 3*(restart + 2) + (restart + 2) * 592 doubles
- *     must fit in the array, otherwise MF_ERR_ARG with a message (e.g. 2D
- *     workloads of ~16k DoFs with restart <= 100);
+ *   - (2*restart + 10) * n_dofs + 3*(restart + 2) + (restart + 2) * MF_REDUCE_BLOCKS
+ *     doubles must fit in the array, otherwise MF_ERR_ARG with a message (e.g.
+ *     2D workloads of ~16k DoFs with restart <= 100); MF_REDUCE_BLOCKS is the
+ *     number of partial sums of the library's dot-product kernels (the same
+ *     constant sizes them);
  *   - per-kernel profiling (mf_profile) must be off (MF_ERR_STATE otherwise).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
@@ -400,6 +420,7 @@ mf_status mf_run_transient(mf_handle h, double* u_n, double* u_nm1, int n_steps,
  * streams, two threads, two handles) race on the array: serialise them.
  * Arguments, results and errors are those of mf_solve_step. */
 #define MF_STATIC_WS_DOUBLES (4u << 20)
+#define MF_REDUCE_BLOCKS 592
 mf_status mf_solve_step_static(mf_handle h, double* up, const mf_solver_opts* so, mf_solve_report* rep,
                                void* stream);
 
@@ -520,6 +541,17 @@ typedef struct {
 } mf_profile_t;
 mf_status mf_profile(mf_handle h, int enable);           /* enable/disable, resets counters */
 mf_status mf_profile_read(mf_handle h, mf_profile_t* out); /* synchronising */
+
+/* mf_fma_peak: the measured FMA issue rate of the current device in FP64
+ * (prec = MF_FP64) or FP32 (MF_FP32), the denominator of the ALU roofline that
+ * bounds the cell and mortar kernels.  One hand-written kernel of independent
+ * FMA chains (8 per thread, 2048 threads per SM, every SM) is launched twice
+ * to warm up and five times between CUDA events on `stream`; *tflops receives
+ * 2 x FMAs / seconds / 1e12 and ms_out (host, may be NULL) the mean launch time.
+ * Synchronising; allocates one small scratch buffer.  MF_ERR_ARG for another
+ * prec or a null tflops, MF_ERR_CUDA on a failed launch.  Not in the paper
+ * (a measurement aid: the paper reports no roofline). */
+mf_status mf_fma_peak(int prec, double* tflops, double* ms_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import MF_FP64, MF_FP32, MF_DF64, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
     MfSolverOpts, MfSolveReport
 
-__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "log_open", "mortar_segments", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
+__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "log_open", "fma_peak", "mortar_segments", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
            "solver_defaults"]
 
 
@@ -166,6 +166,14 @@ def log_open(path):
     """Append one JSON line per library call (solves, transient runs, mesh
     generation, autotuning, checkpoints) to `path`; None turns the log off."""
     _check(_lib.load().mf_log_open(str(path).encode() if path else None), None, "mf_log_open")
+
+
+def fma_peak(prec=MF_FP64, stream=None):
+    """Measured FMA rate of the current device (mf_fma_peak): (TFLOP/s, ms per
+    probe launch) in FP64 or FP32."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(_lib.load().mf_fma_peak(int(prec), C.byref(tf), C.byref(ms), _stream(stream)), None, "mf_fma_peak")
+    return tf.value, ms.value
 
 
 def _host_f64(a):

@@ -21,7 +21,7 @@ EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_mesh_params_defaults", "mf
            "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step",
            "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
            "mf_mg_interpolate", "mf_solve_step_static", "mf_batch_create", "mf_batch_destroy",
-           "mf_batch_apply_jacobian", "mf_batch_solve_step", "mf_batch_last_error", "mf_autotune", "mf_set_cells_per_block", "mf_kinetic_energy", "mf_energy", "mf_wall_loads", "mf_run_transient"]
+           "mf_batch_apply_jacobian", "mf_batch_solve_step", "mf_batch_last_error", "mf_autotune", "mf_set_cells_per_block", "mf_kinetic_energy", "mf_energy", "mf_wall_loads", "mf_run_transient", "mf_fma_peak"]
 PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
               "cell_linearization", "dirichlet", "diagonal"]
 
@@ -142,6 +142,7 @@ def load():
     lib.mf_mg_interpolate.argtypes = [vp, vp, vp, vp]
     lib.mf_profile.argtypes = [vp, i32]
     lib.mf_profile_read.argtypes = [vp, C.POINTER(MfProfile)]
+    lib.mf_fma_peak.argtypes = [i32, C.POINTER(dbl), C.POINTER(dbl), vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("mf_mesh_free", "mf_last_error", "mf_batch_last_error", "mf_solver_defaults",
