@@ -131,6 +131,78 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Point physics of the Jacobian (blocks A-hat..D-hat of Section 2.3, tau
+// frozen) at one Gauss point.  In: reference values v (u_1..u_D, p),
+// reference gradients dv[f][r], reference Hessians of the velocity H[c][e]
+// (symmetric pair order), and the point's coefficients: Ji = J^-1, Wq = det J
+// times the Gauss weight, G = Ji Ji^T (off-diagonals doubled), ct (Laplacian
+// mapping correction), a = u* - u_ALE, gU = grad u*, Rs = R*, tau.  Out: value
+// fluxes fv and reference gradient fluxes Fx, quadrature weight folded in, so
+// that the cell vector is B^T (fv + sum_r Dg_r^T Fx[.][r]).
+template <int D, typename T>
+__device__ __forceinline__ void jac_point(const T (&v)[D + 1], const T (&dv)[D + 1][D], const T (&H)[D][Sym<D>::n],
+                                          const T (&Ji)[D][D], T Wq, const T (&G)[Sym<D>::n], const T (&ct)[D],
+                                          const T (&a)[D], const T (&gU)[D][D], const T (&Rs)[D], T tau, T nu, T a0dt,
+                                          T (&fv)[D + 1], T (&Fx)[D + 1][D]) {
+  T gw[D][D], gr[D], lap[D], gal[D], Rl[D];
+#pragma unroll
+  for (int c = 0; c <= D; ++c)
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      T s = T(0);
+#pragma unroll
+      for (int r = 0; r < D; ++r) s = fma(dv[c][r], Ji[r][m], s);
+      if (c < D) gw[c][m] = s; else gr[m] = s;
+    }
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    T l = T(0);
+#pragma unroll
+    for (int e = 0; e < Sym<D>::n; ++e) l = fma(G[e], H[c][e], l);
+#pragma unroll
+    for (int r = 0; r < D; ++r) l = fma(-ct[r], dv[c][r], l);
+    lap[c] = l;
+    T cv = a0dt * v[c];
+#pragma unroll
+    for (int m = 0; m < D; ++m) cv = fma(a[m], gw[c][m], fma(v[m], gU[c][m], cv));
+    gal[c] = cv;
+    Rl[c] = fma(-nu, l, cv + gr[c]);
+  }
+  // physical flux of grad v: nu grad w - r I + tau (R' (x) a + R* (x) w),
+  // with the quadrature weight W folded into its coefficients before the
+  // J^-1 contraction (W nu, W tau R', W tau R*, W r: fewer FP64 multiplies)
+  const T Wnu = Wq * nu, Wtau = Wq * tau, Wp = Wq * v[D];
+  T WRl[D], WRs[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) { WRl[c] = Wtau * Rl[c]; WRs[c] = Wtau * Rs[c]; }
+  T Fp[D][D];
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int m = 0; m < D; ++m)
+      Fp[c][m] = fma(Wnu, gw[c][m], fma(WRl[c], a[m], WRs[c] * v[m])) - (c == m ? Wp : T(0));
+  T divw = T(0);
+#pragma unroll
+  for (int c = 0; c < D; ++c) { fv[c] = Wq * gal[c]; divw += gw[c][c]; }
+  fv[D] = Wq * divw;
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      T s = Ji[r][0] * Fp[c][0];
+#pragma unroll
+      for (int m = 1; m < D; ++m) s = fma(Ji[r][m], Fp[c][m], s);
+      Fx[c][r] = s;
+    }
+#pragma unroll
+  for (int r = 0; r < D; ++r) {
+    T s = Ji[r][0] * WRl[0];
+#pragma unroll
+    for (int m = 1; m < D; ++m) s = fma(Ji[r][m], WRl[m], s);
+    Fx[D][r] = s;
+  }
+}
+
 // One block's worth of cells (block index `blk`) of the cell Jacobian.  The
 // tables in sm.st must be loaded and visible to the block.
 template <int D, int K, typename T, int CPB = CellCfg<D, K>::CPB>
@@ -261,63 +333,7 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_
     for (int c = 0; c < D; ++c) Rs[c] = ld(CF::RS + c);
     const T tau = ld(CF::TAU);
 
-    T gw[D][D], gr[D], lap[D], gal[D], Rl[D];
-#pragma unroll
-    for (int c = 0; c <= D; ++c)
-#pragma unroll
-      for (int m = 0; m < D; ++m) {
-        T s = T(0);
-#pragma unroll
-        for (int r = 0; r < D; ++r) s = fma(dv[c][r], Ji[r][m], s);
-        if (c < D) gw[c][m] = s; else gr[m] = s;
-      }
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      T l = T(0);
-#pragma unroll
-      for (int e = 0; e < Sym<D>::n; ++e) l = fma(G[e], H[c][e], l);
-#pragma unroll
-      for (int r = 0; r < D; ++r) l = fma(-ct[r], dv[c][r], l);
-      lap[c] = l;
-      T cv = a0dt * v[c];
-#pragma unroll
-      for (int m = 0; m < D; ++m) cv = fma(a[m], gw[c][m], fma(v[m], gU[c][m], cv));
-      gal[c] = cv;
-      Rl[c] = fma(-nu, l, cv + gr[c]);
-    }
-    // physical flux of grad v: nu grad w - r I + tau (R' (x) a + R* (x) w),
-    // with the quadrature weight W folded into its coefficients before the
-    // J^-1 contraction (W nu, W tau R', W tau R*, W r: fewer FP64 multiplies)
-    const T Wnu = Wq * nu, Wtau = Wq * tau, Wp = Wq * v[D];
-    T WRl[D], WRs[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) { WRl[c] = Wtau * Rl[c]; WRs[c] = Wtau * Rs[c]; }
-    T Fp[D][D];
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-#pragma unroll
-      for (int m = 0; m < D; ++m)
-        Fp[c][m] = fma(Wnu, gw[c][m], fma(WRl[c], a[m], WRs[c] * v[m])) - (c == m ? Wp : T(0));
-    T divw = T(0);
-#pragma unroll
-    for (int c = 0; c < D; ++c) { fv[c] = Wq * gal[c]; divw += gw[c][c]; }
-    fv[D] = Wq * divw;
-#pragma unroll
-    for (int c = 0; c < D; ++c)
-#pragma unroll
-      for (int r = 0; r < D; ++r) {
-        T s = Ji[r][0] * Fp[c][0];
-#pragma unroll
-        for (int m = 1; m < D; ++m) s = fma(Ji[r][m], Fp[c][m], s);
-        Fx[c][r] = s;
-      }
-#pragma unroll
-    for (int r = 0; r < D; ++r) {
-      T s = Ji[r][0] * WRl[0];
-#pragma unroll
-      for (int m = 1; m < D; ++m) s = fma(Ji[r][m], WRl[m], s);
-      Fx[D][r] = s;
-    }
+    jac_point<D, T>(v, dv, H, Ji, Wq, G, ct, a, gU, Rs, tau, nu, a0dt, fv, Fx);
   }
   // ---- integrate: gradient fluxes through Dg^T, then B^T to the nodes
 #pragma unroll

@@ -7,6 +7,8 @@
 
 namespace mf {
 
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
 // 1D Lagrange values/derivatives on the Gauss-Lobatto nodes at an arbitrary t.
 template <int N, typename T>
 __device__ __forceinline__ void lagrange_at(const MfTab<T>& tb, T t, T* L, T* dL) {
@@ -63,7 +65,7 @@ struct MortarMap {
   int32_t* mc_cell;   // [M][2] rotor, stator cell
   double* mc_tau;     // [M] face penalty max(tau_rotor, tau_stator)
   double* mc_xi;      // [M][2][N] face coordinate on each side
-  double* mc_ang;     // [M][N] absolute angle of the point
+  double* mc_cs;      // [M][N][2] cos and sin of the point's absolute angle (outward stator normal)
   double* mc_w;       // [M][N] angular weight w_g R L
   const int32_t* ifr; // [n_z][n_R]
   const int32_t* ifs;
@@ -107,7 +109,9 @@ __global__ void k_mortar_map(MortarMap A) {
     const double xr = (h == 0) ? 1.0 - (1.0 - sg) * th / Dl : sg * (Dl - th) / Dl;
     A.mc_xi[(m * 2 + 0) * N + g] = xr;
     A.mc_xi[(m * 2 + 1) * N + g] = xs;
-    A.mc_ang[m * N + g] = A.phi0 + start + sg * L;
+    const double ang = A.phi0 + start + sg * L;
+    A.mc_cs[(m * N + g) * 2 + 0] = cos(ang);
+    A.mc_cs[(m * N + g) * 2 + 1] = sin(ang);
     A.mc_w[m * N + g] = tb.w[g] * A.R * L;
   }
 }
@@ -289,7 +293,7 @@ template <int D, int K> struct MortarCfg {
 
 template <typename T> struct MortarArgs {
   const int32_t* cells;
-  const int32_t* mc_cell; const double* mc_tau; const double* mc_xi; const double* mc_ang; const double* mc_w;
+  const int32_t* mc_cell; const double* mc_tau; const double* mc_xi; const double* mc_cs; const double* mc_w;
   const T* jinv;      // [M][2][NP][D][D]
   int64_t nm;
   const typename IO<T>::type* src; typename IO<T>::type* dst;
@@ -361,144 +365,7 @@ __device__ __forceinline__ void mortar_block(MortarSmem<D, K, T>& S, int64_t blk
   }
   __syncthreads();
   const T tau_f = active ? (T)A.mc_tau[mc] : T(0);
-  if (MODE == 0) {
-    // ---- phase 2a: contract xi_0 -> face layer and normal derivative, per (b1, b2) = q
-    if (a < NP) {
-      const int q = a;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        T dn = T(0);
-#pragma unroll
-        for (int b0 = 0; b0 < N; ++b0) dn = fma(dL0[b0], s_val[lm][s][b0 + N * q][f], dn);
-        s_fn[lm][s][q][f] = dn;
-        s_fa[lm][s][q][f] = s_val[lm][s][fc + N * q][f];
-      }
-    }
-    __syncthreads();
-    // ---- phase 2b: traces at point p = ia + N iz
-    if (a < NP) {
-      const int p = a, ia = p % N, iz = (D == 3) ? p / N : 0;
-      T u[NF], du[NF][D];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        u[f] = T(0);
-#pragma unroll
-        for (int r = 0; r < D; ++r) du[f][r] = T(0);
-      }
-#pragma unroll
-      for (int q = 0; q < NP; ++q) {
-        const int b1 = q % N, b2 = (D == 3) ? q / N : 0;
-        const T l1 = s_L1[lm][s][ia][b1], d1 = s_dL1[lm][s][ia][b1];
-        const T l2 = (D == 3) ? tb.B[iz][b2] : T(1), d2 = (D == 3) ? tb.Dn[iz][b2] : T(0);
-        const T w0 = l1 * l2, w1 = d1 * l2, w2 = l1 * d2;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-          const T fa = s_fa[lm][s][q][f];
-          u[f] = fma(w0, fa, u[f]);
-          du[f][0] = fma(w0, s_fn[lm][s][q][f], du[f][0]);
-          du[f][1] = fma(w1, fa, du[f][1]);
-          if (D == 3) du[f][2] = fma(w2, fa, du[f][2]);
-        }
-      }
-      const T* Ji = A.jinv + ((mc * 2 + s) * NP + p) * D * D;
-      T J[D][D];
-#pragma unroll
-      for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int m = 0; m < D; ++m) J[r][m] = active ? Ji[r * D + m] : T(0);
-#pragma unroll
-      for (int f = 0; f < NF; ++f) s_U[lm][s][p][f] = u[f];
-#pragma unroll
-      for (int c = 0; c < D; ++c)
-#pragma unroll
-        for (int m = 0; m < D; ++m) {
-          T g = T(0);
-#pragma unroll
-          for (int r = 0; r < D; ++r) g = fma(du[c][r], J[r][m], g);
-          s_GU[lm][s][p][c][m] = g;
-        }
-    }
-    __syncthreads();
-    // ---- phase 3: fluxes of side s at its points
-    if (a < NP) {
-      const int p = a, ia = p % N, iz = (D == 3) ? p / N : 0;
-      const int o = 1 - s;
-      const double ang = active ? A.mc_ang[mc * N + ia] : 0.0;
-      double wd = active ? A.mc_w[mc * N + ia] : 0.0;
-      if (D == 3) wd *= TabSel<double>::get(K).w[iz] * A.dz;
-      const T w = (T)wd;
-      const T sg = (s == 0) ? T(1) : T(-1);
-      const T n[3] = {sg * (T)cos(ang), sg * (T)sin(ang), T(0)};
-      T jump[D];
-#pragma unroll
-      for (int c = 0; c < D; ++c) jump[c] = s_U[lm][s][p][c] - s_U[lm][o][p][c];
-      const T pavg = T(0.5) * (s_U[lm][s][p][D] + s_U[lm][o][p][D]);
-      T jn = T(0);
-#pragma unroll
-      for (int c = 0; c < D; ++c) jn = fma(jump[c], n[c], jn);
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        T gn = T(0);
-#pragma unroll
-        for (int m = 0; m < D; ++m) gn = fma(s_GU[lm][s][p][c][m] + s_GU[lm][o][p][c][m], n[m], gn);
-        s_fv[lm][s][p][c] = w * (pavg * n[c] - T(0.5) * A.nu * gn + A.nu * tau_f * jump[c]);
-      }
-      s_fv[lm][s][p][D] = -T(0.5) * w * jn;
-      const T* Ji = A.jinv + ((mc * 2 + s) * NP + p) * D * D;
-      T jin[D];
-#pragma unroll
-      for (int r = 0; r < D; ++r) {
-        T t = T(0);
-#pragma unroll
-        for (int m = 0; m < D; ++m) t = fma(active ? Ji[r * D + m] : T(0), n[m], t);
-        jin[r] = t;
-      }
-#pragma unroll
-      for (int c = 0; c < D; ++c)
-#pragma unroll
-        for (int r = 0; r < D; ++r) s_Fx[lm][s][p][c][r] = -T(0.5) * w * A.nu * jump[c] * jin[r];
-    }
-    __syncthreads();
-    // ---- phase 4a: integrate over the points per face position q = (a1, a2)
-    if (a < NP) {
-      const int q = a, a1 = q % N, a2 = (D == 3) ? q / N : 0;
-      T G[NF], Hn[D];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) G[f] = T(0);
-#pragma unroll
-      for (int c = 0; c < D; ++c) Hn[c] = T(0);
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const int ia = p % N, iz = (D == 3) ? p / N : 0;
-        const T l1 = s_L1[lm][s][ia][a1], d1 = s_dL1[lm][s][ia][a1];
-        const T l2 = (D == 3) ? tb.B[iz][a2] : T(1), d2 = (D == 3) ? tb.Dn[iz][a2] : T(0);
-        const T w0 = l1 * l2, w1 = d1 * l2, w2 = l1 * d2;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          T acc = fma(w0, s_fv[lm][s][p][c], G[c]);
-          acc = fma(w1, s_Fx[lm][s][p][c][1], acc);
-          if (D == 3) acc = fma(w2, s_Fx[lm][s][p][c][D - 1], acc);
-          G[c] = acc;
-          Hn[c] = fma(w0, s_Fx[lm][s][p][c][0], Hn[c]);
-        }
-        G[D] = fma(w0, s_fv[lm][s][p][D], G[D]);
-      }
-#pragma unroll
-      for (int f = 0; f < NF; ++f) s_G[lm][s][q][f] = G[f];
-#pragma unroll
-      for (int c = 0; c < D; ++c) s_H[lm][s][q][c] = Hn[c];
-    }
-    __syncthreads();
-    if (!active) return;
-    // ---- phase 4b: node a = a0 + N q: out = l_a0(face) G_q + l'_a0(face) H_q
-    const int a0 = a % N, q = a / N;
-    T out[NF];
-#pragma unroll
-    for (int c = 0; c < D; ++c) out[c] = fma(L0[a0], s_G[lm][s][q][c], dL0[a0] * s_H[lm][s][q][c]);
-    out[D] = L0[a0] * s_G[lm][s][q][D];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) atomic_add(&A.dst[(int64_t)node * NF + f], out[f]);
-  } else {
+  {
     // ---- diagonal: w nu [tau phi^2 - phi (grad phi . n_s)] on face nodes, per velocity component
     if (!active) return;
     const int a0 = a % N, a1 = (a / N) % N, a2 = a / (N * N);
@@ -508,11 +375,10 @@ __device__ __forceinline__ void mortar_block(MortarSmem<D, K, T>& S, int64_t blk
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       const int ia = p % N, iz = (D == 3) ? p / N : 0;
-      const double ang = A.mc_ang[mc * N + ia];
       double wd = A.mc_w[mc * N + ia];
       if (D == 3) wd *= TabSel<double>::get(K).w[iz] * A.dz;
       const T w = (T)wd;
-      const T n[3] = {sg * (T)cos(ang), sg * (T)sin(ang), T(0)};
+      const T n[3] = {sg * (T)A.mc_cs[(mc * N + ia) * 2], sg * (T)A.mc_cs[(mc * N + ia) * 2 + 1], T(0)};
       const T l1 = s_L1[lm][s][ia][a1], d1 = s_dL1[lm][s][ia][a1];
       const T l2 = (D == 3) ? tb.B[iz][a2] : T(1), d2 = (D == 3) ? tb.Dn[iz][a2] : T(0);
       const T phi = l1 * l2;
@@ -533,10 +399,280 @@ __device__ __forceinline__ void mortar_block(MortarSmem<D, K, T>& S, int64_t blk
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Face terms, MODE 0 (dst += M src), every phase spread over all threads of
+// the half-cell.  Same terms and tables as mortar_block, with the traces and
+// the test-side integration sum-factorised over the two face directions
+// (angular first, then z) and the point data precomputed per rotor angle
+// (cos / sin of the point's angle; the nodal basis is a Kronecker delta on
+// the face and its normal derivative there is the table dLe).  Per side:
+//   2a  face layer fa (all fields) and normal derivative fn (velocity)
+//   2b  traces u and reference velocity gradients du at the points
+//   2c  physical velocity gradients GU = du J^-1
+//   3   fluxes fv, Fx of the face terms at the points
+//   4a  integration against the face test functions: G (values), H (normal
+//       derivative)
+//   4b  node a = a0 + N q: l_a0(face) G_q + l_a0'(face) H_q, scatter-add.
+template <int D, int K, typename T> struct MortarApplySmem {
+  static constexpr int N = K + 1, NPC = ipow(N, D), NP = ipow(N, D - 1), NF = D + 1, MPB = MortarCfg<D, K>::MPB;
+  // three regions reused across phases (lifetimes do not overlap within a region)
+  static constexpr int NV3 = 10, NZ3 = 13;                        // 3D intermediate variants
+  static constexpr int R1 = cmax(cmax(NPC * NF, N * N * NV3), cmax(NP * (NF + D * D), NP * (NF + D)));
+  static constexpr int R2 = cmax(NP * (NF + D) + NP * D * D, N * N * NZ3);
+  static constexpr int R3 = NP * NF + NP * D * D;
+  T r1[MPB][2][R1];   // val | Y | fv, Fx | G, H
+  T r2[MPB][2][R2];   // fa, fn, DU | Z
+  T r3[MPB][2][R3];   // U, GU
+  T L1[MPB][2][N][N];
+  T dL1[MPB][2][N][N];
+};
+
+template <int D, int K, typename T>
+__device__ __forceinline__ void mortar_apply_block(MortarApplySmem<D, K, T>& S, int64_t blk, const MortarArgs<T>& A) {
+  using C = MortarCfg<D, K>;
+  using SM = MortarApplySmem<D, K, T>;
+  constexpr int N = C::N, NPC = C::NPC, NP = C::NP, NF = D + 1, TPM = 2 * NPC;
+  const MfTab<T>& tb = TabSel<T>::get(K);
+  const int lm = threadIdx.x / TPM;
+  const int loc = threadIdx.x % TPM;
+  const int64_t mc = blk * C::MPB + lm;
+  const bool active = mc < A.nm;
+  // region views, per side
+  auto val = [&](int s, int a, int f) -> T& { return S.r1[lm][s][a * NF + f]; };
+  auto fa = [&](int s, int q, int f) -> T& { return S.r2[lm][s][q * NF + f]; };
+  auto fn = [&](int s, int q, int c) -> T& { return S.r2[lm][s][NP * NF + q * D + c]; };
+  auto DU = [&](int s, int p, int c, int r) -> T& { return S.r2[lm][s][NP * (NF + D) + (p * D + c) * D + r]; };
+  auto Y = [&](int s, int ia, int b2, int v) -> T& { return S.r1[lm][s][(ia * N + b2) * SM::NV3 + v]; };
+  auto U = [&](int s, int p, int f) -> T& { return S.r3[lm][s][p * NF + f]; };
+  auto GU = [&](int s, int p, int c, int m) -> T& { return S.r3[lm][s][NP * NF + (p * D + c) * D + m]; };
+  auto FV = [&](int s, int p, int f) -> T& { return S.r1[lm][s][p * NF + f]; };
+  auto FX = [&](int s, int p, int c, int r) -> T& { return S.r1[lm][s][NP * NF + (p * D + c) * D + r]; };
+  auto Z = [&](int s, int ia, int a2, int v) -> T& { return S.r2[lm][s][(ia * N + a2) * SM::NZ3 + v]; };
+  // G, H: in 3D read Z (r2) and go to r1; in 2D they read fv, Fx (r1) and go to r2
+  auto GH = [&](int s) -> T* { return D == 3 ? S.r1[lm][s] : S.r2[lm][s]; };
+  auto G = [&](int s, int q, int f) -> T& { return GH(s)[q * NF + f]; };
+  auto H = [&](int s, int q, int c) -> T& { return GH(s)[NP * NF + q * D + c]; };
+
+  // ---- phase 1: gather both sides (node a of side s per thread), 1D tables along the face
+  int node = 0;
+  {
+    const int s = loc / NPC, a = loc % NPC;
+    if (active) {
+      const int cell = A.mc_cell[2 * mc + s];
+      const int id = A.cells[(int64_t)cell * NPC + a];
+      const bool wall = id < 0;
+      node = wall ? ~id : id;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) val(s, a, f) = from_io<T>(A.src[(int64_t)node * NF + f]);
+      if (wall && A.zero_wall) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) val(s, a, c) = T(0);
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) val(s, a, f) = T(0);
+    }
+    if (a < N) {
+      T L1[N], dL1[N];
+      lagrange_at<N, T>(tb, active ? (T)A.mc_xi[(mc * 2 + s) * N + a] : T(0), L1, dL1);
+#pragma unroll
+      for (int b = 0; b < N; ++b) { S.L1[lm][s][a][b] = L1[b]; S.dL1[lm][s][a][b] = dL1[b]; }
+    }
+  }
+  __syncthreads();
+  // ---- 2a: face layer (xi_0 = 1 rotor, 0 stator) and its normal derivative
+  for (int it = loc; it < 2 * NP * NF; it += TPM) {
+    const int s = it / (NP * NF), q = (it / NF) % NP, f = it % NF;
+    const int fc = (s == 0) ? K : 0;
+    const T v = val(s, fc + N * q, f);
+    T dn = T(0);
+    if (f < D) {
+#pragma unroll
+      for (int b0 = 0; b0 < N; ++b0) dn = fma(tb.dLe[s == 0 ? 1 : 0][b0], val(s, b0 + N * q, f), dn);
+    }
+    fa(s, q, f) = v;
+    if (f < D) fn(s, q, f) = dn;
+  }
+  __syncthreads();
+  if constexpr (D == 3) {
+    // ---- 2b (angular): Y[ia][b2] = {L1 fa (4), dL1 fa (3), L1 fn (3)}
+    for (int it = loc; it < 2 * N * N * SM::NV3; it += TPM) {
+      const int s = it / (N * N * SM::NV3), r = it % (N * N * SM::NV3);
+      const int ia = r / (N * SM::NV3), b2 = (r / SM::NV3) % N, v = r % SM::NV3;
+      T acc = T(0);
+#pragma unroll
+      for (int b1 = 0; b1 < N; ++b1) {
+        const int q = b1 + N * b2;
+        const T x = v < NF ? fa(s, q, v) : v < NF + D ? fa(s, q, v - NF) : fn(s, q, v - NF - D);
+        const T m = (v >= NF && v < NF + D) ? S.dL1[lm][s][ia][b1] : S.L1[lm][s][ia][b1];
+        acc = fma(m, x, acc);
+      }
+      Y(s, ia, b2, v) = acc;
+    }
+    __syncthreads();
+    // ---- 2b (z): u (4), du_0 (3, normal), du_1 (3, angular), du_2 (3, z) at p = ia + N iz
+    for (int it = loc; it < 2 * NP * SM::NZ3; it += TPM) {
+      const int s = it / (NP * SM::NZ3), p = (it / SM::NZ3) % NP, o = it % SM::NZ3;
+      const int ia = p % N, iz = p / N;
+      const int v = o < NF ? o : o < NF + D ? NF + D + (o - NF) : o < NF + 2 * D ? NF + (o - NF - D) : o - NF - 2 * D;
+      T acc = T(0);
+#pragma unroll
+      for (int b2 = 0; b2 < N; ++b2) acc = fma(o < NF + 2 * D ? tb.B[iz][b2] : tb.Dn[iz][b2], Y(s, ia, b2, v), acc);
+      if (o < NF) U(s, p, o) = acc;
+      else DU(s, p, (o - NF) % D, (o - NF) / D) = acc;
+    }
+  } else {
+    // ---- 2b (2D, one face direction): u (3), du_0 (2), du_1 (2) at p = ia
+    constexpr int NO = NF + 2 * D;
+    for (int it = loc; it < 2 * NP * NO; it += TPM) {
+      const int s = it / (NP * NO), p = (it / NO) % NP, o = it % NO;
+      T acc = T(0);
+#pragma unroll
+      for (int b1 = 0; b1 < N; ++b1) {
+        const T x = o < NF ? fa(s, b1, o) : o < NF + D ? fn(s, b1, o - NF) : fa(s, b1, o - NF - D);
+        const T m = o < NF + D ? S.L1[lm][s][p][b1] : S.dL1[lm][s][p][b1];
+        acc = fma(m, x, acc);
+      }
+      if (o < NF) U(s, p, o) = acc;
+      else DU(s, p, (o - NF) % D, (o - NF) / D) = acc;
+    }
+  }
+  __syncthreads();
+  // ---- 2c: physical velocity gradients
+  for (int it = loc; it < 2 * NP * D * D; it += TPM) {
+    const int s = it / (NP * D * D), p = (it / (D * D)) % NP, c = (it / D) % D, m = it % D;
+    const T* Ji = A.jinv + ((mc * 2 + s) * NP + p) * D * D;
+    T g = T(0);
+#pragma unroll
+    for (int r = 0; r < D; ++r) g = fma(DU(s, p, c, r), active ? Ji[r * D + m] : T(0), g);
+    GU(s, p, c, m) = g;
+  }
+  __syncthreads();
+  // ---- 3: fluxes of side s at point p
+  for (int it = loc; it < 2 * NP; it += TPM) {
+    const int s = it / NP, p = it % NP, ia = p % N, iz = (D == 3) ? p / N : 0;
+    const int o = 1 - s;
+    double wd = active ? A.mc_w[mc * N + ia] : 0.0;
+    if (D == 3) wd *= TabSel<double>::get(K).w[iz] * A.dz;
+    const T w = (T)wd;
+    const T sg = (s == 0) ? T(1) : T(-1);
+    const T n[3] = {active ? sg * (T)A.mc_cs[(mc * N + ia) * 2] : T(0),
+                    active ? sg * (T)A.mc_cs[(mc * N + ia) * 2 + 1] : T(0), T(0)};
+    const T tau_f = active ? (T)A.mc_tau[mc] : T(0);
+    T jump[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) jump[c] = U(s, p, c) - U(o, p, c);
+    const T pavg = T(0.5) * (U(s, p, D) + U(o, p, D));
+    T jn = T(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) jn = fma(jump[c], n[c], jn);
+    T fvl[NF];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      T gn = T(0);
+#pragma unroll
+      for (int m = 0; m < D; ++m) gn = fma(GU(s, p, c, m) + GU(o, p, c, m), n[m], gn);
+      fvl[c] = w * (pavg * n[c] - T(0.5) * A.nu * gn + A.nu * tau_f * jump[c]);
+    }
+    fvl[D] = -T(0.5) * w * jn;
+    const T* Ji = A.jinv + ((mc * 2 + s) * NP + p) * D * D;
+    T jin[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      T t = T(0);
+#pragma unroll
+      for (int m = 0; m < D; ++m) t = fma(active ? Ji[r * D + m] : T(0), n[m], t);
+      jin[r] = t;
+    }
+    const T hw = -T(0.5) * w * A.nu;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) FV(s, p, f) = fvl[f];
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int r = 0; r < D; ++r) FX(s, p, c, r) = hw * jump[c] * jin[r];
+  }
+  __syncthreads();
+  if constexpr (D == 3) {
+    // ---- 4a (z): Z[ia][a2] = {B fv (4), B Fx_.1 (3), Dn Fx_.2 (3), B Fx_.0 (3)}
+    for (int it = loc; it < 2 * N * N * SM::NZ3; it += TPM) {
+      const int s = it / (N * N * SM::NZ3), r = it % (N * N * SM::NZ3);
+      const int ia = r / (N * SM::NZ3), a2 = (r / SM::NZ3) % N, v = r % SM::NZ3;
+      T acc = T(0);
+#pragma unroll
+      for (int iz = 0; iz < N; ++iz) {
+        const int p = ia + N * iz;
+        const T x = v < NF ? FV(s, p, v)
+                  : v < NF + D ? FX(s, p, v - NF, 1)
+                  : v < NF + 2 * D ? FX(s, p, v - NF - D, 2) : FX(s, p, v - NF - 2 * D, 0);
+        const T m = (v >= NF + D && v < NF + 2 * D) ? tb.Dn[iz][a2] : tb.B[iz][a2];
+        acc = fma(m, x, acc);
+      }
+      Z(s, ia, a2, v) = acc;
+    }
+    __syncthreads();
+    // ---- 4a (angular): G_q (4), H_q (3) at q = a1 + N a2
+    for (int it = loc; it < 2 * NP * (NF + D); it += TPM) {
+      const int s = it / (NP * (NF + D)), q = (it / (NF + D)) % NP, o = it % (NF + D);
+      const int a1 = q % N, a2 = q / N;
+      T acc = T(0);
+#pragma unroll
+      for (int ia = 0; ia < N; ++ia) {
+        const T l1 = S.L1[lm][s][ia][a1];
+        if (o < D) {
+          acc = fma(l1, Z(s, ia, a2, o) + Z(s, ia, a2, NF + D + o), acc);
+          acc = fma(S.dL1[lm][s][ia][a1], Z(s, ia, a2, NF + o), acc);
+        } else if (o == D) {
+          acc = fma(l1, Z(s, ia, a2, D), acc);
+        } else {
+          acc = fma(l1, Z(s, ia, a2, NF + 2 * D + (o - NF)), acc);
+        }
+      }
+      if (o < NF) G(s, q, o) = acc;
+      else H(s, q, o - NF) = acc;
+    }
+  } else {
+    // ---- 4a (2D): G_q (3), H_q (2) at q = a1
+    for (int it = loc; it < 2 * NP * (NF + D); it += TPM) {
+      const int s = it / (NP * (NF + D)), q = (it / (NF + D)) % NP, o = it % (NF + D);
+      T acc = T(0);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const T l1 = S.L1[lm][s][p][q];
+        if (o < D) acc = fma(S.dL1[lm][s][p][q], FX(s, p, o, 1), fma(l1, FV(s, p, o), acc));
+        else if (o == D) acc = fma(l1, FV(s, p, D), acc);
+        else acc = fma(l1, FX(s, p, o - NF, 0), acc);
+      }
+      if (o < NF) G(s, q, o) = acc;
+      else H(s, q, o - NF) = acc;
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  // ---- 4b: node a = a0 + N q of side s
+  {
+    const int s = loc / NPC, a = loc % NPC;
+    const int a0 = a % N, q = a / N, fc = (s == 0) ? K : 0;
+    const T dl = tb.dLe[s == 0 ? 1 : 0][a0];
+    T out[NF];
+#pragma unroll
+    for (int c = 0; c < D; ++c) out[c] = (a0 == fc) ? fma(dl, H(s, q, c), G(s, q, c)) : dl * H(s, q, c);
+    out[D] = (a0 == fc) ? G(s, q, D) : T(0);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) atomic_add(&A.dst[(int64_t)node * NF + f], out[f]);
+  }
+}
+
 template <int D, int K, typename T, int MODE>
 __global__ void __launch_bounds__(MortarCfg<D, K>::THREADS) k_mortar(MortarArgs<T> A) {
-  __shared__ MortarSmem<D, K, T> S;
-  mortar_block<D, K, T, MODE>(S, blockIdx.x, A);
+  if constexpr (MODE == 0) {
+    __shared__ MortarApplySmem<D, K, T> S;
+    mortar_apply_block<D, K, T>(S, blockIdx.x, A);
+  } else {
+    __shared__ MortarSmem<D, K, T> S;
+    mortar_block<D, K, T, MODE>(S, blockIdx.x, A);
+  }
 }
 
 // Batched mortar terms (MODE 0) over several instances: persistent grid,
@@ -550,7 +686,7 @@ template <typename T> struct MortarBatchTable {
 template <int D, int K, typename T>
 __global__ void __launch_bounds__(MortarCfg<D, K>::THREADS)
 k_mortar_batched(const MortarBatchTable<T>* __restrict__ tab, unsigned long long* __restrict__ counter) {
-  __shared__ MortarSmem<D, K, T> S;
+  __shared__ MortarApplySmem<D, K, T> S;
   __shared__ long long s_tile;
   const int64_t total = tab->first_tile[tab->ninst];
   for (;;) {
@@ -561,7 +697,7 @@ k_mortar_batched(const MortarBatchTable<T>* __restrict__ tab, unsigned long long
     if (tile >= total) break;
     int i = 0;
     while (i + 1 < tab->ninst && tab->first_tile[i + 1] <= tile) ++i;
-    mortar_block<D, K, T, 0>(S, tile - tab->first_tile[i], tab->inst[i]);
+    mortar_apply_block<D, K, T>(S, tile - tab->first_tile[i], tab->inst[i]);
   }
 }
 

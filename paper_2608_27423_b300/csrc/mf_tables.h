@@ -18,6 +18,7 @@ struct MfTab {
   T w[MF_NMAX];             // Gauss weights on [0,1] (sum 1)
   T gll[MF_NMAX];           // Gauss-Lobatto nodes on [0,1]
   T bw[MF_NMAX];            // 1 / prod_{b != a} (gll_a - gll_b)
+  T dLe[2][MF_NMAX];        // dLe[e][a] = l_a'(e): nodal-basis derivatives at the ends xi = 0, 1
 };
 
 namespace mfhost {
@@ -97,7 +98,14 @@ inline void build_tab(int k, MfTab<double>& T) {
   for (int i = 0; i < MF_NMAX; ++i) {
     T.s[i] = i < n ? s[i] : 0; T.w[i] = i < n ? w[i] : 0; T.gll[i] = i < n ? g[i] : 0;
     for (int j = 0; j < MF_NMAX; ++j) T.B[i][j] = T.Dn[i][j] = T.Hn[i][j] = T.Dg[i][j] = 0;
+    T.dLe[0][i] = T.dLe[1][i] = 0;
   }
+  for (int e = 0; e < 2; ++e)
+    for (int a = 0; a < n; ++a) {
+      double v, d1, d2;
+      lagrange(g, n, a, (double)e, v, d1, d2);
+      T.dLe[e][a] = d1;
+    }
   for (int a = 0; a < n; ++a) {
     double den = 1.0;
     for (int b = 0; b < n; ++b) if (b != a) den *= (g[a] - g[b]);
@@ -119,6 +127,7 @@ template <typename T>
 inline void cast_tab(const MfTab<double>& A, MfTab<T>& B) {
   for (int i = 0; i < MF_NMAX; ++i) {
     B.s[i] = T(A.s[i]); B.w[i] = T(A.w[i]); B.gll[i] = T(A.gll[i]); B.bw[i] = T(A.bw[i]);
+    B.dLe[0][i] = T(A.dLe[0][i]); B.dLe[1][i] = T(A.dLe[1][i]);
     for (int j = 0; j < MF_NMAX; ++j) {
       B.B[i][j] = T(A.B[i][j]); B.Dn[i][j] = T(A.Dn[i][j]); B.Hn[i][j] = T(A.Hn[i][j]); B.Dg[i][j] = T(A.Dg[i][j]);
     }

@@ -64,6 +64,12 @@ def test_fullsize_sampled_rows(name):
     g.apply_jacobian(x, y)
     y32 = torch.empty_like(x, dtype=torch.float32)
     g.apply_jacobian(x.float(), y32, prec=MF_FP32)
+    y32l = None
+    if mesh.d == 3 and mesh.k <= 3:                 # the one-cell-per-lane FP32 kernel as well
+        g.set_cells_per_block(MF_FP32, 32)
+        y32l = torch.empty_like(x, dtype=torch.float32)
+        g.apply_jacobian(x.float(), y32l, prec=MF_FP32)
+        g.set_cells_per_block(MF_FP32, 0)
     from paper_2608_27423_b300 import MF_DF64
     ydf = torch.empty_like(x)
     g.apply_jacobian(x, ydf, prec=MF_DF64)
@@ -77,8 +83,11 @@ def test_fullsize_sampled_rows(name):
     ydf = ydf.cpu().numpy()[nodes]
     y32 = y32.double().cpu().numpy()[nodes]
     r = r.cpu().numpy()[nodes]
+    checks = [(ydf, yj, 1e-12), (y, yj, 1e-12), (y32, yj, 1e-5), (r, yr, 1e-12)]
+    if y32l is not None:
+        checks.append((y32l.double().cpu().numpy()[nodes], yj, 1e-5))
     # normwise and element-wise (max-entry error / max entry) on the sampled rows
-    for got, ref, tol in ((ydf, yj, 1e-12), (y, yj, 1e-12), (y32, yj, 1e-5), (r, yr, 1e-12)):
+    for got, ref, tol in checks:
         assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
         assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
     # properties at any size: finite everywhere, wall rows copied

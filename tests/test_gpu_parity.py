@@ -85,6 +85,20 @@ def test_jacobian_fp32_matches_oracle(c):
     assert rel(y.double().cpu().numpy(), y_ref) <= TOL32
 
 
+@pytest.mark.parametrize("c", [c for c in CASES if c["d"] == 3], ids=cid)
+def test_jacobian_fp32_lane_kernel_matches_oracle(c):
+    """The one-cell-per-lane FP32 kernel (3D, k <= 3; FP32 variant of 32 cells
+    per block), ragged last block included."""
+    mesh, prm, f, op, g, T = setup(**c)
+    from paper_2608_27423_b300 import MF_FP32
+    g.set_cells_per_block(MF_FP32, 32)
+    y_ref = op.apply(f["x"])
+    x32 = T(f["x"]).float()
+    y = torch.full_like(x32, float("nan"))
+    g.apply_jacobian(x32, y, prec=MF_FP32)
+    assert rel(y.double().cpu().numpy(), y_ref) <= TOL32
+
+
 @pytest.mark.parametrize("c", CASES, ids=cid)
 def test_jacobian_df64_matches_oracle_at_fp64_bar(c):
     """Double-float applies (FP32 pipes) meet the FP64 bar."""
