@@ -54,6 +54,10 @@ def parse():
                     help="start the transient from rest (u = 0; the blades and walls drive the flow)")
     ap.add_argument("--transient-no-eager", action="store_true", help="time only the graph-replayed steps")
     ap.add_argument("--clocks-dir", default=None, help="where the nvidia-smi clock samples are written (default: temp)")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="profiling aid: run only the Newton-step leg on --workload and print its JSON")
+    ap.add_argument("--solve-variants", default="mixed_fp32_mg,fp64_mg,mixed_fp32_mg_df64_outer",
+                    help="comma list of the solve leg's variants")
     ap.add_argument("--q3-workload", default="3d_q3", help="the Q3 workload of the q3 leg")
     ap.add_argument("--no-q3", action="store_true", help="skip the Q3 leg")
     ap.add_argument("--no-autotune", action="store_true",
@@ -197,8 +201,11 @@ def solve_leg(args, op, mesh, prm, f, T, workload=None):
     res = {"levels": [f"Q{lv.k}:{lv.n_cells}" for lv in levels]}
     sols = {}
     from paper_2608_27423_b300 import MF_DF64
+    wanted = set(args.solve_variants.split(","))
     for name, pcp, outer in (("mixed_fp32_mg", MF_FP32, MF_FP64), ("fp64_mg", MF_FP64, MF_FP64),
                              ("mixed_fp32_mg_df64_outer", MF_FP32, MF_DF64)):
+        if name not in wanted:
+            continue
         up = U0.clone()
         o = solver_defaults(theta=prm["theta"], pc=MF_PC_MG, pc_precision=pcp, newton_rtol=1e-8,
                             max_newton=args.max_newton, lin_rtol=1e-2, restart=30, max_lin_iters=150,
@@ -215,6 +222,8 @@ def solve_leg(args, op, mesh, prm, f, T, workload=None):
         print(f"solve {name}: status {st} {dt_s:.2f}s newton {n_it} "
               f"res {rep.res_norm[0]:.3e} -> {rep.res_norm[n_it]:.3e}", file=sys.stderr, flush=True)
         sols[name] = up
+    if "fp64_mg" not in sols or "mixed_fp32_mg" not in sols:
+        return res
     a, b = sols["fp64_mg"], sols["mixed_fp32_mg"]
     va, vb = a[:, :d], b[:, :d]
     pa, pb = a[:, d] - a[:, d].mean(), b[:, d] - b[:, d].mean()
@@ -645,6 +654,11 @@ def main():
     up_star = T(f["up_star"])
     op.set_history(T(f["u_n"]), T(f["u_nm1"]) if f["u_nm1"] is not None else None)
     op.set_linearization(up_star, prm["theta"])
+    if args.solve_only:
+        if not args.no_autotune:
+            op.autotune()
+        print(json.dumps({"workload": args.workload, "solve": solve_leg(args, op, mesh, prm, f, T)}), flush=True)
+        return
     x = T(f["x"])
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()

@@ -162,6 +162,44 @@ mf_status mf_mesh_read(const mf_mesh* m, double* x0, uint8_t* node_side, uint8_t
                        uint8_t* cell_side, int32_t* iface_rotor, int32_t* iface_stator);
 mf_status mf_mesh_coarsen_map(const mf_mesh_params* fine, mf_mesh_params* coarse, int32_t* parent, uint8_t* child);
 
+/* ---------------------------------------------------------------- z-slab partition (multi-GPU)
+ * mf_mesh_slab: part `part` of a partition of a 3D mesh into n_parts z-slabs
+ * (1 <= n_parts <= n_z), the counterpart of the paper's mesh decomposition
+ * (Section 3.3).  Part p owns the z-layers [floor(p n_z / P), floor((p+1)
+ * n_z / P)) (a cell's layer from the mean z of its nodes).  The rotation axis
+ * is z, so every mortar pair lies in one layer and stays on one part at every
+ * rotor angle.  Parts p and p+1 share the node plane between their layers:
+ * an operator applied on each part gives partial sums on its shared planes,
+ * and one exchange per neighbour completes them (mf_halo_pack on the sender,
+ * mf_halo_add on the receiver).  Outputs (HOST, each may be NULL):
+ *   out        the slab as a mesh of its own (local node numbering in
+ *              ascending global id; its layers' interface rows; height
+ *              H (l1 - l0) / n_z, so the layer height is unchanged);
+ *   info       sizes: nodes, cells, layer range, shared-plane node counts;
+ *   node_global [n_nodes] global id of each local node;
+ *   lo, hi     [n_lo], [n_hi] local ids of the nodes shared with part p-1 /
+ *              p+1, in ascending global id (the neighbour lists the same
+ *              nodes in the same order); lo_wall, hi_wall: 1 for wall nodes.
+ * Call once with out and the arrays NULL to size the arrays.  Errors:
+ * MF_ERR_ARG (2D mesh, part out of range, n_parts > n_z, unequal interface
+ * partitions, an interface cell outside its layer's part).  Host code. */
+typedef struct {
+  int64_t n_nodes, n_cells;
+  int     layer_begin, layer_end;
+  int     n_lo, n_hi;
+} mf_slab_info;
+mf_status mf_mesh_slab(const mf_mesh* m, int n_parts, int part, mf_mesh** out, mf_slab_info* info,
+                       int64_t* node_global, int32_t* lo, int32_t* hi, uint8_t* lo_wall, uint8_t* hi_wall);
+/* Halo exchange kernels (device pointers, asynchronous on `stream`):
+ * mf_halo_pack: buf[i][f] = y[idx[i]][f] for i < n, f < nf (the partial
+ * rows of a shared plane, to send);  mf_halo_add: y[idx[i]][f] += buf[i][f]
+ * (the neighbour's partial rows), except the velocity components of wall
+ * nodes (wall[i] = 1; wall may be NULL), whose identity rows both parts hold
+ * already.  MF_ERR_ARG for null pointers or nf < 1. */
+mf_status mf_halo_pack(const double* y, const int32_t* idx, int64_t n, int nf, double* buf, void* stream);
+mf_status mf_halo_add(double* y, const int32_t* idx, const uint8_t* wall, int64_t n, int nf, const double* buf,
+                      void* stream);
+
 /* ---------------------------------------------------------------- per-call metrics log
  * mf_log_open(path): from now on the mesh generator, mf_solve_step,
  * mf_batch_solve_step, mf_run_transient, mf_autotune and the checkpoint calls
@@ -302,6 +340,10 @@ typedef struct {
                            0 = launch eagerly.  Graphs are skipped while profiling is enabled. */
   int    outer_precision; /* Jacobian applies of the outer FGMRES: MF_FP64 (default) or MF_DF64
                              (FP64-accurate double-float on the FP32 pipes) */
+  int    batch_fallback;  /* mf_batch_solve_step only: 1 = an instance still above tolerance after the
+                             batched iterations (or stopped by the step safeguard) continues alone with
+                             mf_solve_step (restart `restart`, lin_rtol, its own graphs) from its last
+                             iterate, to the same absolute target newton_rtol ||R_0|| (default 1) */
 } mf_solver_opts;
 
 typedef struct {
@@ -312,6 +354,8 @@ typedef struct {
   double lambda_max;          /* estimated spectral radius of D^-1 J */
   double seconds;             /* wall time of the solve (host clock) */
   int    status;              /* mf_status of the solve */
+  int    fallback_newton_iters; /* mf_batch_solve_step: Newton iterations of the adaptive fallback
+                                   (included in newton_iters; 0 when none ran) */
 } mf_solve_report;
 
 void mf_solver_defaults(mf_solver_opts* o);
@@ -327,7 +371,7 @@ mf_status mf_solve_step(mf_handle h, double* up, const mf_solver_opts* so, mf_so
                         void* stream);
 
 /* ---------------------------------------------------------------- energy budget and wall loads
- * (Section 5.3.2 energy balance, Section 5.2.2 torque analysis)
+ * (Section 4.5.2 energy balance, Section 4.4.2 torque analysis)
  *
  * mf_kinetic_energy: ke_dev (device double) = 1/2 int |u|^2 over the mesh at
  * the current geometry (Gauss rule of the operator); needs the geometry cache
@@ -378,7 +422,7 @@ mf_status mf_wall_loads(mf_handle h, const double* up, const uint8_t* group, int
  * term, so the torque includes the BDF inertia of the wall rows) and the
  * step's residual reduction ||R_end|| / ||R_start|| (0 in record 0).  The
  * numerical dissipation of the energy balance follows on the host:
- * eps_n T-bar = power - dissipation_sym - dE/dt (Section 5.3.2).  Errors:
+ * eps_n T-bar = power - dissipation_sym - dE/dt (Section 4.5.2).  Errors:
  * MF_ERR_ARG (dt = 0, counts out of range), MF_ERR_STATE (MG without levels). */
 typedef struct {
   double kinetic_energy;      /* 1/2 int |u|^2 */
@@ -469,6 +513,11 @@ mf_status mf_batch_apply_jacobian(mf_batch* b, const void* const* xs, void* cons
  * value, else the instance keeps its previous iterate and stops
  * (line_search = 0: full steps; only a non-finite ||R_i|| stops an instance).  reps (host, n entries, may be NULL): per instance
  * res_norm[0..newton_iters], lin_iters, wall seconds of the call, status.
+ * With so->batch_fallback = 1 (default), an instance that has not converged
+ * when the batched loop ends continues alone with mf_solve_step (adaptive
+ * FGMRES(restart), same preconditioner) from its last iterate until ||R_i|| <=
+ * newton_rtol ||R_i,0||; its report then covers both parts
+ * (fallback_newton_iters says how many iterations the fallback took).
  * Returns MF_OK when every instance converged, otherwise the first failing
  * instance's status (MF_ERR_NOT_CONVERGED or MF_ERR_NAN; ups then hold the
  * last accepted iterates).  Errors: MF_ERR_ARG (null pointers,

@@ -106,7 +106,7 @@ class Problem:
 
     def energy(self, up):
         """Energy budget terms of the discrete velocity u_h at the current
-        geometry, by the operator's Gauss rule (Section 5.3.2, energy balance):
+        geometry, by the operator's Gauss rule (Section 4.5.2, energy balance):
         kinetic energy 1/2 int |u_h|^2; viscous dissipation of the Laplacian
         viscous form, nu int grad u_h : grad u_h; and the paper's dissipation
         -tau : grad u with the deviatoric stress tau = -nu (grad u + grad u^T),

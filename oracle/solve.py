@@ -70,8 +70,8 @@ class Operator:
 
     def wall_loads(self, up, group=None, n_groups=2):
         """Loads of the walls on the fluid from the consistent reactions
-        (torque at the impeller, Section 5.2.2; power at the wall in the
-        energy balance, Section 5.3.2).  r = the residual rows of the volume and
+        (torque at the impeller, Section 4.4.2; power at the wall in the
+        energy balance, Section 4.5.2).  r = the residual rows of the volume and
         mortar terms without the Dirichlet replacement; on a wall node i it
         equals int_wall t . phi_i, t the traction the wall exerts on the fluid.
         Summed over a group of wall nodes: force sum_i r_i, torque about the

@@ -12,7 +12,7 @@ from . import _lib
 from ._lib import MF_FP64, MF_FP32, MF_DF64, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
     MfSolverOpts, MfSolveReport
 
-__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "log_open", "fma_peak", "mortar_segments", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
+__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "log_open", "fma_peak", "mortar_segments", "slab_partition", "halo_pack", "halo_add", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
            "solver_defaults"]
 
 
@@ -89,27 +89,75 @@ def rotor_stator_mesh(**params):
     mp = C.c_void_p()
     _check(lib.mf_mesh_rotor_stator(C.byref(p), C.byref(mp)), None, "mf_mesh_rotor_stator")
     try:
-        d, k, n_R, n_z = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-        nn, nc = C.c_int64(), C.c_int64()
-        _check(lib.mf_mesh_sizes(mp, C.byref(d), C.byref(k), C.byref(nn), C.byref(nc), C.byref(n_R), C.byref(n_z)),
-               None, "mf_mesh_sizes")
-        d, k, nn, nc, n_R, n_z = d.value, k.value, nn.value, nc.value, n_R.value, n_z.value
-        nrs = C.c_int()
-        _check(lib.mf_mesh_interface(mp, None, C.byref(nrs), None), None, "mf_mesh_interface")
-        n_Rs = nrs.value
-        x0 = np.empty((nn, d))
-        ns, wall = np.empty(nn, np.uint8), np.empty(nn, np.uint8)
-        cells = np.empty((nc, (k + 1) ** d), np.int32)
-        cs = np.empty(nc, np.uint8)
-        ifr, ifs = np.empty((n_z, n_R), np.int32), np.empty((n_z, n_Rs), np.int32)
-        _check(lib.mf_mesh_read(mp, _np_ptr(x0), _np_ptr(ns), _np_ptr(wall), _np_ptr(cells), _np_ptr(cs),
-                                _np_ptr(ifr), _np_ptr(ifs)), None, "mf_mesh_read")
+        m = _read_mesh(mp, R=p.R, H=p.H, phi0=p.phi0)
     finally:
         lib.mf_mesh_free(mp)
-    pd = {f: getattr(p, f) for f, _ in _lib.MfMeshParams._fields_}
+    m.params = {f: getattr(p, f) for f, _ in _lib.MfMeshParams._fields_}
+    return m
+
+
+def _read_mesh(mp, R, H, phi0):
+    """Host arrays of an mf_mesh (mf_mesh_sizes, mf_mesh_interface, mf_mesh_read) as a Mesh."""
+    lib = _lib.load()
+    d, k, n_R, n_z = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    nn, nc = C.c_int64(), C.c_int64()
+    _check(lib.mf_mesh_sizes(mp, C.byref(d), C.byref(k), C.byref(nn), C.byref(nc), C.byref(n_R), C.byref(n_z)),
+           None, "mf_mesh_sizes")
+    d, k, nn, nc, n_R, n_z = d.value, k.value, nn.value, nc.value, n_R.value, n_z.value
+    nrs = C.c_int()
+    _check(lib.mf_mesh_interface(mp, None, C.byref(nrs), None), None, "mf_mesh_interface")
+    n_Rs = nrs.value
+    x0 = np.empty((nn, d))
+    ns, wall = np.empty(nn, np.uint8), np.empty(nn, np.uint8)
+    cells = np.empty((nc, (k + 1) ** d), np.int32)
+    cs = np.empty(nc, np.uint8)
+    ifr, ifs = np.empty((n_z, n_R), np.int32), np.empty((n_z, n_Rs), np.int32)
+    _check(lib.mf_mesh_read(mp, _np_ptr(x0), _np_ptr(ns), _np_ptr(wall), _np_ptr(cells), _np_ptr(cs),
+                            _np_ptr(ifr), _np_ptr(ifs)), None, "mf_mesh_read")
     return Mesh(d=d, k=k, x0=x0, cells=cells, cell_side=cs, node_side=ns, wall=wall, iface_rotor=ifr,
-                iface_stator=ifs, R=p.R, n_R=n_R, n_z=n_z, H=(p.H if d == 3 else 1.0), phi0=p.phi0, params=pd,
+                iface_stator=ifs, R=R, n_R=n_R, n_z=n_z, H=(H if d == 3 else 1.0), phi0=phi0, params=None,
                 n_R_stator=n_Rs)
+
+
+def slab_partition(mesh, n_parts, part):
+    """Part `part` of the z-slab partition of a 3D mesh into n_parts parts
+    (mf_mesh_slab).  Returns (slab Mesh, plan) with plan = dict(node_global
+    [n_nodes] int64, lo / hi [n] int32 local ids of the nodes shared with the
+    part below / above (ascending global id), lo_wall / hi_wall uint8,
+    layer_begin, layer_end)."""
+    lib = _lib.load()
+    gm = _mesh_handle(mesh)
+    sm = C.c_void_p()
+    try:
+        info = _lib.MfSlabInfo()
+        _check(lib.mf_mesh_slab(gm, int(n_parts), int(part), None, C.byref(info), None, None, None, None, None),
+               None, "mf_mesh_slab")
+        ng = np.empty(info.n_nodes, np.int64)
+        lo, hi = np.empty(info.n_lo, np.int32), np.empty(info.n_hi, np.int32)
+        lw, hw = np.empty(info.n_lo, np.uint8), np.empty(info.n_hi, np.uint8)
+        _check(lib.mf_mesh_slab(gm, int(n_parts), int(part), C.byref(sm), C.byref(info), _np_ptr(ng), _np_ptr(lo),
+                                _np_ptr(hi), _np_ptr(lw), _np_ptr(hw)), None, "mf_mesh_slab")
+        H = float(mesh.H) * (info.layer_end - info.layer_begin) / int(mesh.n_z)
+        slab = _read_mesh(sm, R=float(mesh.R), H=H, phi0=float(mesh.phi0))
+    finally:
+        lib.mf_mesh_free(gm)
+        if sm.value:
+            lib.mf_mesh_free(sm)
+    plan = dict(node_global=ng, lo=lo, hi=hi, lo_wall=lw, hi_wall=hw, layer_begin=info.layer_begin,
+                layer_end=info.layer_end)
+    return slab, plan
+
+
+def halo_pack(y, idx, buf, stream=None):
+    """buf[i, :] = y[idx[i], :] (mf_halo_pack; device FP64 tensors, idx int32)."""
+    _check(_lib.load().mf_halo_pack(_ptr(y), _ptr(idx), int(idx.numel()), int(y.shape[-1]), _ptr(buf),
+                                    _stream(stream)), None, "mf_halo_pack")
+
+
+def halo_add(y, idx, wall, buf, stream=None):
+    """y[idx[i], :] += buf[i, :] except wall velocity rows (mf_halo_add)."""
+    _check(_lib.load().mf_halo_add(_ptr(y), _ptr(idx), _ptr(wall) if wall is not None else None, int(idx.numel()),
+                                   int(y.shape[-1]), _ptr(buf), _stream(stream)), None, "mf_halo_add")
 
 
 def mortar_segments(n_R, n_Rs, theta):

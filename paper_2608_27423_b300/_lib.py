@@ -21,7 +21,8 @@ EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_mesh_params_defaults", "mf
            "mf_residual", "mf_apply_jacobian", "mf_diagonal", "mf_solver_defaults", "mf_solve_step",
            "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
            "mf_mg_interpolate", "mf_solve_step_static", "mf_batch_create", "mf_batch_destroy",
-           "mf_batch_apply_jacobian", "mf_batch_solve_step", "mf_batch_last_error", "mf_autotune", "mf_set_cells_per_block", "mf_kinetic_energy", "mf_energy", "mf_wall_loads", "mf_run_transient", "mf_fma_peak"]
+           "mf_batch_apply_jacobian", "mf_batch_solve_step", "mf_batch_last_error", "mf_autotune", "mf_set_cells_per_block", "mf_kinetic_energy", "mf_energy", "mf_wall_loads", "mf_run_transient", "mf_fma_peak",
+           "mf_mesh_slab", "mf_halo_pack", "mf_halo_add"]
 PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
               "cell_linearization", "dirichlet", "diagonal"]
 
@@ -47,13 +48,14 @@ class MfSolverOpts(C.Structure):
                 ("pc", C.c_int), ("pc_precision", C.c_int), ("cheb_degree", C.c_int),
                 ("cheb_lo", C.c_double), ("theta", C.c_double), ("inner_iters", C.c_int),
                 ("line_search", C.c_int), ("mg_smooth", C.c_int), ("mg_coarse_iters", C.c_int),
-                ("deflate_pressure", C.c_int), ("use_graphs", C.c_int), ("outer_precision", C.c_int)]
+                ("deflate_pressure", C.c_int), ("use_graphs", C.c_int), ("outer_precision", C.c_int),
+                ("batch_fallback", C.c_int)]
 
 
 class MfSolveReport(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("lin_iters_total", C.c_int), ("lin_iters", C.c_int * 64),
                 ("res_norm", C.c_double * 65), ("lambda_max", C.c_double), ("seconds", C.c_double),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("fallback_newton_iters", C.c_int)]
 
 
 STEP_RECORD_FIELDS = ("kinetic_energy", "dissipation", "dissipation_sym", "torque_still", "torque_moving", "power",
@@ -71,6 +73,11 @@ class MfTuneResult(C.Structure):
 
 class MfProfile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
+
+
+class MfSlabInfo(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_cells", C.c_int64), ("layer_begin", C.c_int), ("layer_end", C.c_int),
+                ("n_lo", C.c_int), ("n_hi", C.c_int)]
 
 
 class MfError(RuntimeError):
@@ -143,6 +150,9 @@ def load():
     lib.mf_profile.argtypes = [vp, i32]
     lib.mf_profile_read.argtypes = [vp, C.POINTER(MfProfile)]
     lib.mf_fma_peak.argtypes = [i32, C.POINTER(dbl), C.POINTER(dbl), vp]
+    lib.mf_mesh_slab.argtypes = [vp, i32, i32, C.POINTER(vp), C.POINTER(MfSlabInfo), vp, vp, vp, vp, vp]
+    lib.mf_halo_pack.argtypes = [vp, vp, i64, i32, vp, vp]
+    lib.mf_halo_add.argtypes = [vp, vp, vp, i64, i32, vp, vp]
     for name in EXPORTS:
         f = getattr(lib, name)
         if name not in ("mf_mesh_free", "mf_last_error", "mf_batch_last_error", "mf_solver_defaults",

@@ -14,6 +14,7 @@
 
 #include "../../include/mf.h"
 #include "mf_cell.cuh"
+#include "mf_lane.cuh"
 #include "mf_mortar.cuh"
 #include "mf_small.cuh"
 #include "mf_pmg.cuh"
@@ -113,7 +114,7 @@ struct mf_ctx {
   int32_t *cells = nullptr, *wall = nullptr, *ifr = nullptr, *ifs = nullptr;
   double *tau_r = nullptr, *tau_s = nullptr;
   int32_t* mc_cell = nullptr;
-  double *mc_tau = nullptr, *mc_xi = nullptr, *mc_ang = nullptr, *mc_w = nullptr;
+  double *mc_tau = nullptr, *mc_xi = nullptr, *mc_cs = nullptr, *mc_w = nullptr;
   double* mg_jinv64 = nullptr;   // face geometry J^-1 at the mortar points [M][2][NP][d][d]
   float* mg_jinv32 = nullptr;
   df* mg_jinvdf = nullptr;       // double-float copies for MF_DF64 (built on demand)
@@ -123,6 +124,8 @@ struct mf_ctx {
   double* react = nullptr;             // reaction rows scratch of mf_wall_loads [n_dofs]
   double* cache64 = nullptr;
   float* cache32 = nullptr;
+  float* lcache32 = nullptr;           // 3D, k <= 3: FP32 cache in the lane layout (k_cell_jac_lane)
+  int32_t* lcells = nullptr;           // 3D, k <= 3: lane-interleaved cell table
   Workspace ws;
   MgLink mg;
   cudaStream_t cap_stream = nullptr;   // library stream for graph capture
@@ -212,6 +215,10 @@ static void launch_state(mf_ctx* h, int mode, const double* up, double* dst, cud
   else k_cell_state<D, K, 1><<<g, C::THREADS, 0, st>>>(A);
 }
 
+// The one-cell-per-lane FP32 kernel (mf_lane.cuh) exists for 3D, k = 1..3;
+// for those, FP32 variant 2 is that kernel (32 cells per block).
+static constexpr bool lane_kernel_available(int d, int k) { return d == 3 && k >= 1 && k <= 3; }
+
 // Cells-per-block variants of the cell Jacobian that mf_autotune times, per
 // (D, K): index 0 is the default CellCfg<D, K>::CPB (about 256 threads), 1 and
 // 2 a smaller and a larger block.  (D, K) without own variants repeat the
@@ -221,7 +228,9 @@ template <int D, int K> struct CpbVariants {
 };
 template <> struct CpbVariants<3, 2> { static constexpr int n = 3, v1 = 4, v2 = 16; };   // 108 / 243 / 432 threads
 template <> struct CpbVariants<3, 3> { static constexpr int n = 3, v1 = 2, v2 = 6; };    // 128 / 256 / 384 threads
-template <int D, int K> static int cpb_variant(int i) {
+template <> struct CpbVariants<3, 1> { static constexpr int n = 3, v1 = 16, v2 = 32; };  // 128 / 256 / 256 threads
+template <int D, int K> static int cpb_variant(int i, bool fp32 = false) {
+  if (fp32 && i == 2 && lane_kernel_available(D, K)) return LaneCfg<K <= 3 ? K : 1>::CB;
   return i == 1 ? CpbVariants<D, K>::v1 : i == 2 ? CpbVariants<D, K>::v2 : CellCfg<D, K>::CPB;
 }
 
@@ -232,6 +241,37 @@ static void launch_jac_cpb(mf_ctx* h, const T* cache, const typename IO<T>::type
                                                                                 (T)h->nu, (T)h->a0dt);
 }
 
+template <int D, int K>
+static void launch_lane_cells(mf_ctx* h, cudaStream_t st) {
+  if constexpr (D == 3 && K <= 3) {
+    const int64_t total = (h->nc + 31) / 32 * LaneCfg<K>::NQ * 32;
+    k_lane_cells<K><<<std::min<int64_t>(nblk(total, 256), 148 * 16), 256, 0, st>>>(h->cells, h->nc, h->lcells);
+  }
+}
+
+template <int D, int K>
+static void launch_lane_cache(mf_ctx* h, cudaStream_t st) {
+  if constexpr (D == 3 && K <= 3) {
+    const int64_t total = (h->nc + 31) / 32 * LaneCache::NF * LaneCfg<K>::NQ * 32;
+    k_lane_cache<K><<<std::min<int64_t>(nblk(total, 256), 148 * 16), 256, 0, st>>>(h->cache64, h->nc, h->lcache32);
+  }
+}
+
+template <int K>
+static void launch_jac_lane(mf_ctx* h, const float* x, float* y, cudaStream_t st) {
+  using L = LaneCfg<K>;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    cudaFuncSetAttribute(k_cell_jac_lane<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
+    attr_set[dev] = true;
+  }
+  k_cell_jac_lane<K><<<nblk(h->nc, L::CB), L::THREADS, L::SMEM, st>>>(h->lcells, h->nc, h->lcache32,
+                                                                      reinterpret_cast<const float4*>(x), y,
+                                                                      (float)h->nu, (float)h->a0dt);
+}
+
 template <int D, int K, typename T>
 static void launch_jac(mf_ctx* h, const T* cache, const typename IO<T>::type* x, typename IO<T>::type* y,
                        cudaStream_t st) {
@@ -239,7 +279,11 @@ static void launch_jac(mf_ctx* h, const T* cache, const typename IO<T>::type* x,
   if constexpr (std::is_same<T, df>::value) {
     launch_jac_cpb<D, K, T, CellCfg<D, K>::CPB>(h, cache, x, y, st);    // double-float: default only
   } else {
-    switch (h->cpb_sel[std::is_same<T, double>::value ? 0 : 1]) {
+    const int sel = h->cpb_sel[std::is_same<T, double>::value ? 0 : 1];
+    if constexpr (std::is_same<T, float>::value && D == 3 && K <= 3) {
+      if (sel == 2) { launch_jac_lane<K>(h, x, y, st); return; }
+    }
+    switch (sel) {
       case 1: launch_jac_cpb<D, K, T, CpbVariants<D, K>::v1>(h, cache, x, y, st); break;
       case 2: launch_jac_cpb<D, K, T, CpbVariants<D, K>::v2>(h, cache, x, y, st); break;
       default: launch_jac_cpb<D, K, T, CellCfg<D, K>::CPB>(h, cache, x, y, st); break;
@@ -254,7 +298,7 @@ static void launch_mortar(mf_ctx* h, int mode, const typename IO<T>::type* src, 
   A.cells = h->cells; A.mc_cell = h->mc_cell; A.mc_tau = h->mc_tau; A.mc_xi = h->mc_xi;
   A.jinv = std::is_same<T, double>::value ? (const T*)h->mg_jinv64
          : std::is_same<T, float>::value ? (const T*)h->mg_jinv32 : (const T*)h->mg_jinvdf;
-  A.mc_ang = h->mc_ang; A.mc_w = h->mc_w; A.nm = h->nm; A.src = src; A.dst = dst; A.nu = (T)h->nu;
+  A.mc_cs = h->mc_cs; A.mc_w = h->mc_w; A.nm = h->nm; A.src = src; A.dst = dst; A.nu = (T)h->nu;
   A.dz = h->H / h->n_z; A.zero_wall = zero_wall;
   using C = MortarCfg<D, K>;
   const unsigned g = nblk(h->nm, C::MPB);
@@ -280,7 +324,7 @@ static void launch_penalty(mf_ctx* h, cudaStream_t st) {
 template <int K>
 static void launch_map(mf_ctx* h, cudaStream_t st) {
   MortarMap A;
-  A.mc_cell = h->mc_cell; A.mc_tau = h->mc_tau; A.mc_xi = h->mc_xi; A.mc_ang = h->mc_ang; A.mc_w = h->mc_w;
+  A.mc_cell = h->mc_cell; A.mc_tau = h->mc_tau; A.mc_xi = h->mc_xi; A.mc_cs = h->mc_cs; A.mc_w = h->mc_w;
   A.ifr = h->ifr; A.ifs = h->ifs; A.tau_r = h->tau_r; A.tau_s = h->tau_s; A.n_R = h->n_R; A.n_z = h->n_z;
   A.R = h->R; A.phi0 = h->phi0; A.theta = h->theta; A.theta_dev = h->theta_on_dev ? h->d_theta : nullptr;
   k_mortar_map<K><<<nblk(h->nm, 128), 128, 0, st>>>(A);
@@ -329,6 +373,7 @@ extern "C" void mf_mesh_free(mf_mesh* m) { delete m; }
 
 #include "mf_meshgen.inc"
 #include "mf_checkpoint.inc"
+#include "mf_slab.inc"
 
 // ------------------------------------------------------------------ create
 static void free_ws(Workspace& w) {
@@ -349,8 +394,9 @@ extern "C" mf_status mf_destroy(mf_handle h) {
   if (h->d_theta && h->own_theta) cudaFree(h->d_theta);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
-                  h->mc_cell, h->mc_tau, h->mc_xi, h->mc_ang, h->mc_w, h->ht, h->g, h->cache64, h->cache32,
-                  h->mg_jinv64, h->mg_jinv32, h->mg_jinvdf, h->cachedf, h->react, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32};
+                  h->mc_cell, h->mc_tau, h->mc_xi, h->mc_cs, h->mc_w, h->ht, h->g, h->cache64, h->cache32,
+                  h->mg_jinv64, h->mg_jinv32, h->mg_jinvdf, h->cachedf, h->react, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32,
+                  h->lcache32, h->lcells};
   for (void* p : ptrs) if (p) cudaFree(p);
   free_ws(h->ws);
   delete h;
@@ -419,10 +465,14 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
     ALLOC2(h->cells, nc * npc); ALLOC2(h->wall, wl.size()); ALLOC2(h->ifr, h->nif); ALLOC2(h->ifs, h->nif);
     ALLOC2(h->tau_r, h->nif); ALLOC2(h->tau_s, h->nif);
     ALLOC2(h->mc_cell, h->nm * 2); ALLOC2(h->mc_tau, h->nm); ALLOC2(h->mc_xi, h->nm * 2 * (k + 1));
-    ALLOC2(h->mc_ang, h->nm * (k + 1)); ALLOC2(h->mc_w, h->nm * (k + 1));
+    ALLOC2(h->mc_cs, h->nm * (k + 1) * 2); ALLOC2(h->mc_w, h->nm * (k + 1));
     ALLOC2(h->mg_jinv64, h->nm * 2 * ipow(k + 1, m->d - 1) * m->d * m->d);
     ALLOC2(h->mg_jinv32, h->nm * 2 * ipow(k + 1, m->d - 1) * m->d * m->d);
     ALLOC2(h->ht, nn * d); ALLOC2(h->cache64, (size_t)h->ncache * nc * npc); ALLOC2(h->cache32, (size_t)h->ncache * nc * npc);
+    if (lane_kernel_available(h->d, h->k)) {
+      const size_t padded = (nc + 31) / 32 * 32;
+      ALLOC2(h->lcells, padded * npc); ALLOC2(h->lcache32, (size_t)LaneCache::NF * padded * npc);
+    }
   } while (0);
 #undef ALLOC2
   if (cudaMemcpy(h->x0, m->x0.data(), nn * d * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -434,6 +484,7 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
       cudaMemcpy(h->ifs, m->ifs.data(), h->nif * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(h->ht, 0, nn * d * 8) != cudaSuccess)
     return fail(MF_ERR_CUDA);
+  if (h->lcells) MF_DISPATCH(h->d, h->k, (launch_lane_cells<D, K>(h, 0)));
   // geometry at theta = 0, penalties (rotation-invariant), mortar cells
   if (h->d == 2) k_rotate<2><<<nblk(h->nn, 256), 256>>>(h->x0, h->node_side, h->x, h->nn, 1.0, 0.0, nullptr);
   else k_rotate<3><<<nblk(h->nn, 256), 256>>>(h->x0, h->node_side, h->x, h->nn, 1.0, 0.0, nullptr);
@@ -494,6 +545,7 @@ extern "C" mf_status mf_set_linearization(mf_handle h, const double* up_star, do
   MF_DISPATCH(h->d, h->k, (launch_state<D, K>(h, 0, up_star, nullptr, st)));
   const int64_t ncv = (int64_t)h->ncache * h->nc * ipow(h->k + 1, h->d);
   k_cast<double, float><<<nblk(ncv, 256), 256, 0, st>>>(h->cache64, h->cache32, ncv);
+  if (h->lcache32) MF_DISPATCH(h->d, h->k, (launch_lane_cache<D, K>(h, st)));
   CK(cudaGetLastError());
   h->have_lin = true;
   h->df_valid = false;
@@ -775,7 +827,7 @@ static mf_status fill_batch_tables(mf_batch* b, const void* const* xs, void* con
     MortarArgs<T>& A = hm->inst[i];
     A.cells = c->cells; A.mc_cell = c->mc_cell; A.mc_tau = c->mc_tau; A.mc_xi = c->mc_xi;
     A.jinv = f64 ? (const T*)c->mg_jinv64 : (const T*)c->mg_jinv32;
-    A.mc_ang = c->mc_ang; A.mc_w = c->mc_w; A.nm = c->nm; A.src = (const T*)xs[i]; A.dst = (T*)ys[i];
+    A.mc_cs = c->mc_cs; A.mc_w = c->mc_w; A.nm = c->nm; A.src = (const T*)xs[i]; A.dst = (T*)ys[i];
     A.nu = (T)c->nu; A.dz = c->H / c->n_z; A.zero_wall = 1;
     hm->first_tile[i + 1] = hm->first_tile[i] + (c->nm + mpb - 1) / mpb;
   }
