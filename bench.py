@@ -53,6 +53,12 @@ def parse():
     ap.add_argument("--transient-rest", action="store_true",
                     help="start the transient from rest (u = 0; the blades and walls drive the flow)")
     ap.add_argument("--transient-no-eager", action="store_true", help="time only the graph-replayed steps")
+    ap.add_argument("--transient-step-rtol", type=float, default=0.0,
+                    help="per-step convergence control: more Newton iterations while ||R|| > this x ||R_0|| (0: off)")
+    ap.add_argument("--transient-max-newton", type=int, default=8, help="Newton iterations per step at most (control)")
+    ap.add_argument("--transient-oracle-slab", type=int, default=0,
+                    help="compare the final state's energy terms on one z-slab of a partition into this many parts "
+                         "(the middle part) with the oracle (0: off)")
     ap.add_argument("--clocks-dir", default=None, help="where the nvidia-smi clock samples are written (default: temp)")
     ap.add_argument("--solve-only", action="store_true",
                     help="profiling aid: run only the Newton-step leg on --workload and print its JSON")
@@ -254,10 +260,12 @@ def transient_leg(args, op, mesh, prm, f, T):
     if not args.transient_rest:
         u0[:, :d] = f["u_n"]
         u0[mesh.wall.astype(bool), :d] = 0.0
-    o = solver_defaults(pc=MF_PC_MG, pc_precision=MF_FP32, mg_smooth=4, mg_coarse_iters=40)
+    o = solver_defaults(pc=MF_PC_MG, pc_precision=MF_FP32, mg_smooth=4, mg_coarse_iters=40,
+                        step_rtol=args.transient_step_rtol, max_newton=args.transient_max_newton)
     nn, nk = args.transient_newton, args.transient_krylov
     out = {"steps": args.transient, "newton_per_step": nn, "fgmres_per_newton": nk,
-           "start": "rest" if args.transient_rest else "smooth random u^n (walls zero)"}
+           "start": "rest" if args.transient_rest else "smooth random u^n (walls zero)",
+           "step_rtol": args.transient_step_rtol, "max_newton_per_step": args.transient_max_newton}
     modes = (("graph", True),) if args.transient_no_eager else (("graph", True), ("eager", False))
     for label, graph in modes:
         un, unm1 = T(u0), T(u0)
@@ -273,7 +281,43 @@ def transient_leg(args, op, mesh, prm, f, T):
             for key in ("kinetic_energy", "dissipation_sym", "torque_moving", "power"):
                 out[key] = [float(x) for x in rec[key]]
             out["residual_reduction_per_step"] = [float(x) for x in rec["residual_reduction"][1:]]
+            out["newton_iters_per_step"] = [int(x) for x in rec["newton_iters"][1:]]
+            ke = np.asarray(rec["kinetic_energy"])
+            # energy balance of each step (Section 4.5.2): numerical dissipation rate = wall power -
+            # viscous dissipation - dE/dt (BDF1 difference of the recorded kinetic energies)
+            out["numerical_dissipation_rate"] = [float(rec["power"][i] - rec["dissipation_sym"][i]
+                                                       - (ke[i] - ke[i - 1]) / prm["dt"]) for i in range(1, len(ke))]
+            final = (un, unm1)
+    out["dofs_steps_per_s"] = out["graph"]["dofs_steps_per_s"]
+    if args.transient_oracle_slab > 0:
+        theta_end = prm["theta"] + args.transient * prm["omega"] * prm["dt"]
+        out["oracle_slab"] = energy_on_slab(mesh, prm, final[0].cpu().numpy(), theta_end,
+                                            args.transient_oracle_slab, T)
     return out
+
+
+def energy_on_slab(mesh, prm, up, theta, n_parts, T):
+    """Energy terms (kinetic energy, both dissipation forms) of the state `up`
+    restricted to the middle z-slab of an n_parts partition, by the library
+    (an operator on the slab mesh, mf_energy) and by the oracle
+    (Problem.energy on the same slab), at rotor angle theta."""
+    import torch
+    from oracle.fem import Problem
+    from paper_2608_27423_b300 import RotorStatorOperator, slab_partition
+    part = n_parts // 2
+    slab, plan = slab_partition(mesh, n_parts, part)
+    ups = np.ascontiguousarray(up[plan["node_global"]])
+    op = RotorStatorOperator(slab, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
+    op.set_linearization(T(ups), theta)
+    e = torch.empty(3, dtype=torch.float64, device=T(ups[:1]).device)
+    op.energy(T(ups), e)
+    gpu = [float(v) for v in e.cpu().numpy()]
+    t0 = time.perf_counter()
+    ref = list(Problem(slab, prm["nu"], prm["omega"], prm["dt"], prm["bdf"], theta).energy(ups))
+    return {"parts": n_parts, "part": part, "layers": [plan["layer_begin"], plan["layer_end"]],
+            "cells": slab.n_cells, "fraction_of_cells": slab.n_cells / mesh.n_cells,
+            "gpu": gpu, "oracle": ref, "oracle_seconds": time.perf_counter() - t0,
+            "max_rel_diff": max(abs(a - b) / abs(b) for a, b in zip(gpu, ref) if b != 0.0)}
 
 
 # --------------------------------------------------------------------- batched sweep
@@ -665,8 +709,9 @@ def main():
     n_dofs = op.n_dofs
     d, k = mesh.d, mesh.k
     # launch shape of the cell Jacobian picked by measurement (cells per block, FP64 and FP32)
-    default_tune = {p: {"cells_per_block": [], "ms": [], "chosen": 9 if k == 2 else 4, "from_cache": False}
-                    for p in ("fp64", "fp32")}
+    default_tune = {"fp64": {"cells_per_block": [], "ms": [], "chosen": 9 if k == 2 else 4, "from_cache": False},
+                    "fp32": {"cells_per_block": [], "ms": [], "chosen": 32 if d == 3 and k <= 3 else
+                             (9 if k == 2 else 4), "from_cache": False}}
     if args.no_autotune:
         tune = default_tune
     else:

@@ -96,6 +96,16 @@ mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const double* x0,
                               double R, int n_R, int n_z, double H, double phi0,
                               const int32_t* iface_rotor, const int32_t* iface_stator,
                               mf_mesh** out);
+/* mf_mesh_from_arrays_ex: the same with n_R_stator stator interface cells per
+ * layer (iface_stator [n_z][n_R_stator]), possibly different from the rotor's
+ * n_R (a general interface; the paper restricts itself to equal partitions,
+ * Section 3.1 and its conclusions).  n_R_stator = n_R is mf_mesh_from_arrays. */
+mf_status mf_mesh_from_arrays_ex(int d, int k, int64_t n_nodes, const double* x0,
+                                 const uint8_t* node_side, const uint8_t* wall,
+                                 int64_t n_cells, const int32_t* cells, const uint8_t* cell_side,
+                                 double R, int n_R, int n_R_stator, int n_z, double H, double phi0,
+                                 const int32_t* iface_rotor, const int32_t* iface_stator,
+                                 mf_mesh** out);
 void mf_mesh_free(mf_mesh* m);
 
 /* mf_mesh_rotor_stator: generate a merged rotor-stator mesh (Section 3.1: the
@@ -119,10 +129,10 @@ void mf_mesh_free(mf_mesh* m);
  * mf_mesh_params_defaults: d 3, k 2, m 8, n_r 2, n_s 4, n_z 8, R 0.5, R_out 1,
  * H 1, sq 0.55, phi0 -pi/4, no blades, equal partitions.
  * n_R_stator > 0 gives the stator its own number of interface cells per layer
- * (unequal partitions, beyond the paper's equal-partition restriction); such
- * meshes can be generated, read and coarsened-mapped only as equal ones can't
- * (mf_mesh_coarsen_map rejects them), and mf_create rejects them with
- * MF_ERR_ARG until the mortar kernels support them.
+ * (unequal partitions, beyond the paper's equal-partition restriction).  The
+ * operator supports such meshes: its mortar cells are then the n_R +
+ * n_R_stator segments per layer between consecutive rotor and stator vertices
+ * (see mf_mortar_segments); mf_mesh_coarsen_map and mf_mesh_slab reject them.
  * mf_mesh_sizes / mf_mesh_read: the mesh's sizes and a copy of its arrays into
  * caller HOST buffers sized as in mf_mesh_from_arrays (any pointer may be NULL).
  * mf_mesh_coarsen_map: the parameters of the uniformly coarsened mesh (every
@@ -344,6 +354,9 @@ typedef struct {
                              batched iterations (or stopped by the step safeguard) continues alone with
                              mf_solve_step (restart `restart`, lin_rtol, its own graphs) from its last
                              iterate, to the same absolute target newton_rtol ||R_0|| (default 1) */
+  double step_rtol;       /* mf_run_transient only: > 0 turns on per-step convergence control (after
+                             newton_iters iterations, one more at a time, up to max_newton per step,
+                             while ||R|| > step_rtol ||R_0|| of the step); 0 = fixed iterations (default) */
 } mf_solver_opts;
 
 typedef struct {
@@ -415,6 +428,10 @@ mf_status mf_wall_loads(mf_handle h, const double* up, const uint8_t* group, int
  * precision; Chebyshev is not supported); then u_nm1 <- u_n, u_n <- solution.
  * No step waits on the host, so with use_graph = 1 one step is captured as a
  * CUDA graph (on a library stream) and replayed n_steps times on `stream`.
+ * With so->step_rtol > 0 (convergence control) a step is three graphs: the
+ * start with newton_iters iterations, then one more iteration at a time while
+ * ||R|| > step_rtol ||R_0|| of the step (at most so->max_newton iterations in
+ * all; the host reads two norms per check), then the end of the step.
  * u_n, u_nm1: device [n_nodes][d+1] FP64 (u_nm1 unused for BDF1).  On return
  * (synchronising) rec_host[0..n_steps] (host, may be NULL) holds the record of
  * the initial state and of each step's solution: energy terms as mf_energy,
@@ -432,6 +449,7 @@ typedef struct {
   double torque_moving;       /* z torque of the walls moving with the rotor on the fluid */
   double power;               /* power of all walls on the fluid */
   double residual_reduction;  /* ||R_end|| / ||R_start|| of the step */
+  double newton_iters;        /* Newton iterations the step took (0 in record 0) */
 } mf_step_record;
 mf_status mf_run_transient(mf_handle h, double* u_n, double* u_nm1, int n_steps, double theta0, int newton_iters,
                            int krylov_iters, const mf_solver_opts* so, int use_graph, mf_step_record* rec_host,
@@ -529,10 +547,14 @@ mf_status mf_batch_solve_step(mf_batch* b, double* const* ups, const double* the
 const char* mf_batch_last_error(mf_batch* b);
 
 /* ---------------------------------------------------------------- launch-shape autotuning
- * The cell Jacobian kernel runs one thread per Gauss point and several cells
- * per block; the 3D Q2 and Q3 kernels are compiled for three cells-per-block
- * values (Q2: 9 (default), 4, 16; Q3: 4 (default), 2, 6), other (d, k) for the
- * default only.  mf_autotune times every variant of the FP64 and of the FP32
+ * The FP64 cell Jacobian kernel runs one thread per Gauss point and several
+ * cells per block; the 3D Q1, Q2 and Q3 kernels are compiled for three
+ * cells-per-block values (Q1: 32 (default), 16, 32; Q2: 9 (default), 4, 16;
+ * Q3: 4 (default), 2, 6), other (d, k) for the default only.  The FP32
+ * variants of 3D Q1-Q3 are the one-cell-per-lane kernel (32 cells per block;
+ * the default from 148 x 32 cells up) and the per-point kernel with its
+ * default (the default below that size) and smaller block (Q1: 32, 16; Q2:
+ * 9, 4; Q3: 4, 2).  mf_autotune times every variant of the FP64 and of the FP32
  * kernel on this handle's mesh and current linearisation (CUDA events, 3
  * warm-up and 20 timed launches each, on `stream`) and keeps the fastest for
  * this handle's later applies.  res (host, may be NULL) receives two entries,

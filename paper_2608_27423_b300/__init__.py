@@ -193,8 +193,6 @@ def coarsen_map(**params):
 def _mesh_handle(mesh):
     """An mf_mesh (host copy) of a mesh object; free it with mf_mesh_free."""
     lib = _lib.load()
-    if getattr(mesh, "n_R_stator", 0) not in (0, int(mesh.n_R)):
-        raise MfError("unequal interface partitions: the operator supports equal rotor/stator partitions only")
     x0 = np.ascontiguousarray(mesh.x0, dtype=np.float64)
     ns = np.ascontiguousarray(mesh.node_side, dtype=np.uint8)
     wall = np.ascontiguousarray(mesh.wall, dtype=np.uint8)
@@ -203,10 +201,11 @@ def _mesh_handle(mesh):
     ifr = np.ascontiguousarray(mesh.iface_rotor, dtype=np.int32)
     ifs = np.ascontiguousarray(mesh.iface_stator, dtype=np.int32)
     mp = C.c_void_p()
-    _check(lib.mf_mesh_from_arrays(int(mesh.d), int(mesh.k), x0.shape[0], _np_ptr(x0), _np_ptr(ns), _np_ptr(wall),
-                                   cells.shape[0], _np_ptr(cells), _np_ptr(cs), float(mesh.R), int(mesh.n_R),
-                                   int(mesh.n_z), float(mesh.H), float(mesh.phi0), _np_ptr(ifr), _np_ptr(ifs),
-                                   C.byref(mp)), None, "mf_mesh_from_arrays")
+    n_Rs = int(ifs.shape[1]) if ifs.ndim == 2 else int(mesh.n_R)
+    _check(lib.mf_mesh_from_arrays_ex(int(mesh.d), int(mesh.k), x0.shape[0], _np_ptr(x0), _np_ptr(ns), _np_ptr(wall),
+                                      cells.shape[0], _np_ptr(cells), _np_ptr(cs), float(mesh.R), int(mesh.n_R), n_Rs,
+                                      int(mesh.n_z), float(mesh.H), float(mesh.phi0), _np_ptr(ifr), _np_ptr(ifs),
+                                      C.byref(mp)), None, "mf_mesh_from_arrays_ex")
     return mp
 
 

@@ -22,7 +22,7 @@ EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_mesh_params_defaults", "mf
            "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
            "mf_mg_interpolate", "mf_solve_step_static", "mf_batch_create", "mf_batch_destroy",
            "mf_batch_apply_jacobian", "mf_batch_solve_step", "mf_batch_last_error", "mf_autotune", "mf_set_cells_per_block", "mf_kinetic_energy", "mf_energy", "mf_wall_loads", "mf_run_transient", "mf_fma_peak",
-           "mf_mesh_slab", "mf_halo_pack", "mf_halo_add"]
+           "mf_mesh_slab", "mf_halo_pack", "mf_halo_add", "mf_mesh_from_arrays_ex"]
 PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
               "cell_linearization", "dirichlet", "diagonal"]
 
@@ -49,7 +49,7 @@ class MfSolverOpts(C.Structure):
                 ("cheb_lo", C.c_double), ("theta", C.c_double), ("inner_iters", C.c_int),
                 ("line_search", C.c_int), ("mg_smooth", C.c_int), ("mg_coarse_iters", C.c_int),
                 ("deflate_pressure", C.c_int), ("use_graphs", C.c_int), ("outer_precision", C.c_int),
-                ("batch_fallback", C.c_int)]
+                ("batch_fallback", C.c_int), ("step_rtol", C.c_double)]
 
 
 class MfSolveReport(C.Structure):
@@ -59,7 +59,7 @@ class MfSolveReport(C.Structure):
 
 
 STEP_RECORD_FIELDS = ("kinetic_energy", "dissipation", "dissipation_sym", "torque_still", "torque_moving", "power",
-                      "residual_reduction")
+                      "residual_reduction", "newton_iters")
 
 
 class MfStepRecord(C.Structure):
@@ -98,6 +98,8 @@ def load():
     vp, i64, dbl, i32 = C.c_void_p, C.c_int64, C.c_double, C.c_int
     lib.mf_mesh_from_arrays.argtypes = [i32, i32, i64, vp, vp, vp, i64, vp, vp, dbl, i32, i32, dbl, dbl, vp, vp,
                                         C.POINTER(vp)]
+    lib.mf_mesh_from_arrays_ex.argtypes = [i32, i32, i64, vp, vp, vp, i64, vp, vp, dbl, i32, i32, i32, dbl, dbl, vp,
+                                           vp, C.POINTER(vp)]
     lib.mf_mesh_free.argtypes = [vp]
     lib.mf_mesh_free.restype = None
     lib.mf_mesh_params_defaults.argtypes = [C.POINTER(MfMeshParams)]

@@ -21,6 +21,10 @@
 #pragma once
 #include "mf_cell.cuh"
 
+#ifndef MF_LANE_MINB_Q2
+#define MF_LANE_MINB_Q2 2     // Q2: two 288-thread blocks per SM (96 registers, no spills)
+#endif
+
 namespace mf {
 
 template <int K> struct LaneCfg {
@@ -28,7 +32,7 @@ template <int K> struct LaneCfg {
   static constexpr int CB = 32;                 // cells per block: one per lane
   static constexpr int THREADS = N2 * CB;       // one warp per cross-section position
   static constexpr int PLANES = 21;             // shared planes of NQ x CB floats
-  static constexpr int MINB = THREADS <= 128 ? 4 : THREADS <= 288 ? 2 : 1;   // resident blocks asked of ptxas
+  static constexpr int MINB = THREADS <= 128 ? 4 : THREADS <= 288 ? MF_LANE_MINB_Q2 : 1;   // resident blocks asked of ptxas
   static constexpr size_t SMEM = sizeof(float) * (size_t)PLANES * NQ * CB + sizeof(float) * 3 * N * N;
 };
 

@@ -103,7 +103,9 @@ struct mf_ctx {
   int bdf = 1;
   double R = 0, H = 1, phi0 = 0, theta = 0;
   int n_R = 0, n_z = 1;
-  int64_t nm = 0, nwall = 0, nif = 0;
+  int n_Rs = 0;                        // stator interface cells per layer (equal to n_R in the paper's case)
+  int64_t nm = 0, nwall = 0, nif = 0, nif_s = 0;
+  SegTable seg{nullptr, nullptr, nullptr, nullptr, nullptr};   // unequal partitions: segments of one layer
   int64_t nmwall = 0;  // the last nmwall entries of `wall` move with the rotor (blade walls)
   bool have_lin = false;
   int ncache = 0;
@@ -164,6 +166,9 @@ struct ProfScope {
 
 static inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+// grid of the grid-stride vector kernels (256 threads): about 4 entries per
+// thread, at most 8 blocks per SM
+static inline unsigned vgrid(int64_t n) { return (unsigned)std::min<int64_t>(148 * 8, std::max<int64_t>(1, (n + 1023) / 1024)); }
 
 static mf_status upload_tables(mf_ctx* h) {
   int dev = 0;
@@ -216,7 +221,8 @@ static void launch_state(mf_ctx* h, int mode, const double* up, double* dst, cud
 }
 
 // The one-cell-per-lane FP32 kernel (mf_lane.cuh) exists for 3D, k = 1..3;
-// for those, FP32 variant 2 is that kernel (32 cells per block).
+// for those it is the default FP32 variant (index 0, 32 cells per block), and
+// the per-point kernel's default and smaller blocks are variants 1 and 2.
 static constexpr bool lane_kernel_available(int d, int k) { return d == 3 && k >= 1 && k <= 3; }
 
 // Cells-per-block variants of the cell Jacobian that mf_autotune times, per
@@ -230,7 +236,8 @@ template <> struct CpbVariants<3, 2> { static constexpr int n = 3, v1 = 4, v2 = 
 template <> struct CpbVariants<3, 3> { static constexpr int n = 3, v1 = 2, v2 = 6; };    // 128 / 256 / 384 threads
 template <> struct CpbVariants<3, 1> { static constexpr int n = 3, v1 = 16, v2 = 32; };  // 128 / 256 / 256 threads
 template <int D, int K> static int cpb_variant(int i, bool fp32 = false) {
-  if (fp32 && i == 2 && lane_kernel_available(D, K)) return LaneCfg<K <= 3 ? K : 1>::CB;
+  if (fp32 && lane_kernel_available(D, K))
+    return i == 0 ? LaneCfg<K <= 3 ? K : 1>::CB : i == 1 ? CellCfg<D, K>::CPB : CpbVariants<D, K>::v1;
   return i == 1 ? CpbVariants<D, K>::v1 : i == 2 ? CpbVariants<D, K>::v2 : CellCfg<D, K>::CPB;
 }
 
@@ -239,6 +246,13 @@ static void launch_jac_cpb(mf_ctx* h, const T* cache, const typename IO<T>::type
                            cudaStream_t st) {
   k_cell_jac<D, K, T, CPB><<<nblk(h->nc, CPB), CPB * CellCfg<D, K>::NQ, 0, st>>>(h->cells, h->nc, cache, x, y,
                                                                                 (T)h->nu, (T)h->a0dt);
+}
+
+// Default FP32 variant: the one-cell-per-lane kernel where it exists and the
+// mesh gives every SM at least one of its 32-cell blocks, else the per-point
+// kernel (small coarse multigrid levels launch faster with its smaller blocks).
+static int default_fp32_variant(int d, int k, int64_t nc) {
+  return lane_kernel_available(d, k) && nc < 148 * 32 ? 1 : 0;
 }
 
 template <int D, int K>
@@ -279,9 +293,10 @@ static void launch_jac(mf_ctx* h, const T* cache, const typename IO<T>::type* x,
   if constexpr (std::is_same<T, df>::value) {
     launch_jac_cpb<D, K, T, CellCfg<D, K>::CPB>(h, cache, x, y, st);    // double-float: default only
   } else {
-    const int sel = h->cpb_sel[std::is_same<T, double>::value ? 0 : 1];
+    int sel = h->cpb_sel[std::is_same<T, double>::value ? 0 : 1];
     if constexpr (std::is_same<T, float>::value && D == 3 && K <= 3) {
-      if (sel == 2) { launch_jac_lane<K>(h, x, y, st); return; }
+      if (sel == 0) { launch_jac_lane<K>(h, x, y, st); return; }
+      sel = sel == 1 ? 0 : 1;                  // per-point kernel: default, then the smaller block
     }
     switch (sel) {
       case 1: launch_jac_cpb<D, K, T, CpbVariants<D, K>::v1>(h, cache, x, y, st); break;
@@ -316,9 +331,9 @@ static void launch_cell_diag(mf_ctx* h, const T* cache, T* diag, cudaStream_t st
 
 template <int D, int K>
 static void launch_penalty(mf_ctx* h, cudaStream_t st) {
-  const int64_t nif = (int64_t)h->n_z * h->n_R;
+  const int64_t nif = (int64_t)h->n_z * h->n_R, nifs = (int64_t)h->n_z * h->n_Rs;
   k_penalty<D, K><<<nblk(nif, 64), 64, 0, st>>>(h->cells, h->x, h->ifr, nif, 0, h->F, h->tau_r);
-  k_penalty<D, K><<<nblk(nif, 64), 64, 0, st>>>(h->cells, h->x, h->ifs, nif, 1, h->F, h->tau_s);
+  k_penalty<D, K><<<nblk(nifs, 64), 64, 0, st>>>(h->cells, h->x, h->ifs, nifs, 1, h->F, h->tau_s);
 }
 
 template <int K>
@@ -327,6 +342,11 @@ static void launch_map(mf_ctx* h, cudaStream_t st) {
   A.mc_cell = h->mc_cell; A.mc_tau = h->mc_tau; A.mc_xi = h->mc_xi; A.mc_cs = h->mc_cs; A.mc_w = h->mc_w;
   A.ifr = h->ifr; A.ifs = h->ifs; A.tau_r = h->tau_r; A.tau_s = h->tau_s; A.n_R = h->n_R; A.n_z = h->n_z;
   A.R = h->R; A.phi0 = h->phi0; A.theta = h->theta; A.theta_dev = h->theta_on_dev ? h->d_theta : nullptr;
+  if (h->n_Rs != h->n_R) {
+    k_mortar_segments<<<1, 1, 0, st>>>(h->seg, h->n_R, h->n_Rs, h->theta, A.theta_dev);
+    k_mortar_map_general<K><<<nblk(h->nm, 128), 128, 0, st>>>(A, h->seg, h->n_Rs);
+    return;
+  }
   k_mortar_map<K><<<nblk(h->nm, 128), 128, 0, st>>>(A);
 }
 
@@ -342,9 +362,18 @@ extern "C" mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const do
                                          const uint8_t* wall, int64_t n_cells, const int32_t* cells,
                                          const uint8_t* cell_side, double R, int n_R, int n_z, double H, double phi0,
                                          const int32_t* iface_rotor, const int32_t* iface_stator, mf_mesh** out) {
+  return mf_mesh_from_arrays_ex(d, k, n_nodes, x0, node_side, wall, n_cells, cells, cell_side, R, n_R, n_R, n_z, H,
+                                phi0, iface_rotor, iface_stator, out);
+}
+
+extern "C" mf_status mf_mesh_from_arrays_ex(int d, int k, int64_t n_nodes, const double* x0, const uint8_t* node_side,
+                                            const uint8_t* wall, int64_t n_cells, const int32_t* cells,
+                                            const uint8_t* cell_side, double R, int n_R, int n_R_stator, int n_z,
+                                            double H, double phi0, const int32_t* iface_rotor,
+                                            const int32_t* iface_stator, mf_mesh** out) {
   if (!out || !x0 || !node_side || !wall || !cells || !cell_side || !iface_rotor || !iface_stator) return MF_ERR_ARG;
-  if ((d != 2 && d != 3) || k < 1 || k > MF_KMAX || n_nodes <= 0 || n_cells <= 0 || n_R < 1 || n_z < 1 ||
-      !(R > 0) || (d == 3 && !(H > 0)))
+  if ((d != 2 && d != 3) || k < 1 || k > MF_KMAX || n_nodes <= 0 || n_cells <= 0 || n_R < 1 || n_R_stator < 1 ||
+      n_z < 1 || !(R > 0) || (d == 3 && !(H > 0)))
     return MF_ERR_ARG;
   if (n_nodes >= (int64_t)1 << 31) return MF_ERR_ARG;
   if (d == 2) n_z = 1;
@@ -352,6 +381,7 @@ extern "C" mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const do
   mf_mesh* m = new mf_mesh();
   m->d = d; m->k = k; m->nn = n_nodes; m->nc = n_cells; m->R = R; m->H = (d == 2 ? 1.0 : H); m->phi0 = phi0;
   m->n_R = n_R; m->n_z = n_z;
+  m->n_Rs = n_R_stator == n_R ? 0 : n_R_stator;
   m->x0.assign(x0, x0 + n_nodes * d);
   m->node_side.assign(node_side, node_side + n_nodes);
   m->wall.assign(wall, wall + n_nodes);
@@ -360,11 +390,13 @@ extern "C" mf_status mf_mesh_from_arrays(int d, int k, int64_t n_nodes, const do
   m->cells.assign(cells, cells + n_cells * npc);
   m->cell_side.assign(cell_side, cell_side + n_cells);
   m->ifr.assign(iface_rotor, iface_rotor + (int64_t)n_z * n_R);
-  m->ifs.assign(iface_stator, iface_stator + (int64_t)n_z * n_R);
+  m->ifs.assign(iface_stator, iface_stator + (int64_t)n_z * n_R_stator);
   for (int32_t c : m->cells)
     if (c < 0 || c >= n_nodes) { delete m; return MF_ERR_ARG; }
   for (int64_t i = 0; i < (int64_t)n_z * n_R; ++i)
-    if (m->ifr[i] < 0 || m->ifr[i] >= n_cells || m->ifs[i] < 0 || m->ifs[i] >= n_cells) { delete m; return MF_ERR_ARG; }
+    if (m->ifr[i] < 0 || m->ifr[i] >= n_cells) { delete m; return MF_ERR_ARG; }
+  for (int64_t i = 0; i < (int64_t)n_z * n_R_stator; ++i)
+    if (m->ifs[i] < 0 || m->ifs[i] >= n_cells) { delete m; return MF_ERR_ARG; }
   *out = m;
   return MF_OK;
 }
@@ -396,7 +428,7 @@ extern "C" mf_status mf_destroy(mf_handle h) {
   void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
                   h->mc_cell, h->mc_tau, h->mc_xi, h->mc_cs, h->mc_w, h->ht, h->g, h->cache64, h->cache32,
                   h->mg_jinv64, h->mg_jinv32, h->mg_jinvdf, h->cachedf, h->react, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32,
-                  h->lcache32, h->lcells};
+                  h->lcache32, h->lcells, h->seg.start, h->seg.len, h->seg.rstart, h->seg.jr, h->seg.js};
   for (void* p : ptrs) if (p) cudaFree(p);
   free_ws(h->ws);
   delete h;
@@ -427,7 +459,6 @@ static mf_status apply_angle(mf_ctx* h, double theta, cudaStream_t st) {
 extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega, double dt, int bdf,
                                const mf_options* opt, mf_handle* out) {
   if (!m || !out) return MF_ERR_ARG;
-  if (m->n_Rs != 0 && m->n_Rs != m->n_R) return MF_ERR_ARG;   // unequal partitions: no operator yet
   if (k != m->k || !(nu >= 0) || !std::isfinite(omega) || !(dt >= 0) || (bdf != 1 && bdf != 2)) return MF_ERR_ARG;
   mf_ctx* h = new mf_ctx();
   h->d = m->d; h->k = k; h->nn = m->nn; h->nc = m->nc; h->ndof = m->nn * (m->d + 1);
@@ -438,9 +469,12 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
   h->a0dt = dt > 0 ? h->alpha[0] / dt : 0.0;
   h->inv_dt2 = dt > 0 ? 1.0 / (dt * dt) : 0.0;
   h->R = m->R; h->H = m->H; h->phi0 = m->phi0; h->n_R = m->n_R; h->n_z = m->n_z;
-  h->nm = (int64_t)m->n_z * m->n_R * 2;
+  h->n_Rs = m->n_Rs > 0 ? m->n_Rs : m->n_R;
+  h->nm = (int64_t)m->n_z * (m->n_R + h->n_Rs);      // equal partitions: two halves per stator cell
   h->nif = (int64_t)m->n_z * m->n_R;
+  h->nif_s = (int64_t)m->n_z * h->n_Rs;
   h->ncache = (m->d == 2) ? Cache<2>::NF : Cache<3>::NF;
+  h->cpb_sel[1] = default_fp32_variant(m->d, k, m->nc);
   h->nb = MF_REDUCE_BLOCKS;
   mf_status s = upload_tables(h);
   if (s != MF_OK) { mf_destroy(h); return s; }
@@ -462,8 +496,13 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
   if (cudaMalloc((void**)&(p), sizeof(*(p)) * std::max<size_t>(1, (size_t)(cnt))) != cudaSuccess) \
     return fail(MF_ERR_OOM);
     ALLOC2(h->x0, nn * d); ALLOC2(h->x, nn * d); ALLOC2(h->node_side, nn); ALLOC2(h->cell_side, nc);
-    ALLOC2(h->cells, nc * npc); ALLOC2(h->wall, wl.size()); ALLOC2(h->ifr, h->nif); ALLOC2(h->ifs, h->nif);
-    ALLOC2(h->tau_r, h->nif); ALLOC2(h->tau_s, h->nif);
+    ALLOC2(h->cells, nc * npc); ALLOC2(h->wall, wl.size()); ALLOC2(h->ifr, h->nif); ALLOC2(h->ifs, h->nif_s);
+    ALLOC2(h->tau_r, h->nif); ALLOC2(h->tau_s, h->nif_s);
+    if (h->n_Rs != h->n_R) {
+      const size_t ns = (size_t)h->n_R + h->n_Rs;
+      ALLOC2(h->seg.start, ns); ALLOC2(h->seg.len, ns); ALLOC2(h->seg.rstart, ns); ALLOC2(h->seg.jr, ns);
+      ALLOC2(h->seg.js, ns);
+    }
     ALLOC2(h->mc_cell, h->nm * 2); ALLOC2(h->mc_tau, h->nm); ALLOC2(h->mc_xi, h->nm * 2 * (k + 1));
     ALLOC2(h->mc_cs, h->nm * (k + 1) * 2); ALLOC2(h->mc_w, h->nm * (k + 1));
     ALLOC2(h->mg_jinv64, h->nm * 2 * ipow(k + 1, m->d - 1) * m->d * m->d);
@@ -481,7 +520,7 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
       cudaMemcpy(h->cells, cells.data(), nc * npc * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       (wl.size() && cudaMemcpy(h->wall, wl.data(), wl.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
       cudaMemcpy(h->ifr, m->ifr.data(), h->nif * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(h->ifs, m->ifs.data(), h->nif * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->ifs, m->ifs.data(), h->nif_s * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(h->ht, 0, nn * d * 8) != cudaSuccess)
     return fail(MF_ERR_CUDA);
   if (h->lcells) MF_DISPATCH(h->d, h->k, (launch_lane_cells<D, K>(h, 0)));

@@ -117,6 +117,81 @@ __global__ void k_mortar_map(MortarMap A) {
 }
 
 // ---------------------------------------------------------------------------
+// General interfaces (n_R rotor and n_Rs stator cells per layer, Section 3.2's
+// mortar cells with the paper's equal-partition restriction lifted): the
+// circle is cut at every rotor vertex theta + 2 pi i / n_R and every stator
+// vertex 2 pi j / n_Rs (angles from phi0), giving n_R + n_Rs segments per
+// layer, of zero length where a rotor and a stator vertex coincide (their
+// points get zero weights).  One thread merges the two sorted vertex
+// sequences (stator first on ties) into the segment table: start angle,
+// length, rotor cell, stator cell and the rotor cell's start angle.  The
+// angle comes from theta_dev when set (graph replays).
+struct SegTable {
+  double* start; double* len; double* rstart; int32_t* jr; int32_t* js;
+};
+
+__global__ void k_mortar_segments(SegTable S, int n_R, int n_Rs, double theta, const double* __restrict__ theta_dev) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const double two_pi = 2.0 * M_PI, Dr = two_pi / n_R, Ds = two_pi / n_Rs;
+  const double th = theta_dev ? *theta_dev : theta;
+  const double sf = floor(th / Dr);
+  double tp = th - sf * Dr;                         // first rotor vertex in [0, Dr)
+  if (tp < 0.0) tp = 0.0;
+  if (tp >= Dr) tp = 0.0;
+  long long si = (long long)sf % n_R;
+  if (si < 0) si += n_R;
+  auto rcell = [&](int rank) { int c = (int)(((long long)rank - si) % n_R); return c < 0 ? c + n_R : c; };
+  // the rotor cell covering angle 0 starts at the last rotor vertex, wrapped below 0
+  int cur_r = rcell(n_R - 1), cur_s = n_Rs - 1;
+  double cur_rstart = tp + (n_R - 1) * Dr - two_pi;
+  int i = 0, j = 0;
+  const int nseg = n_R + n_Rs;
+  for (int t = 0; t < nseg; ++t) {
+    const double ar = tp + i * Dr, as = j * Ds;
+    double a;
+    if (j < n_Rs && (i >= n_R || as <= ar)) { a = as; cur_s = j; ++j; }
+    else { a = ar; cur_r = rcell(i); cur_rstart = ar; ++i; }
+    S.start[t] = a; S.jr[t] = cur_r; S.js[t] = cur_s; S.rstart[t] = cur_rstart;
+  }
+  for (int t = 0; t < nseg; ++t) {
+    const double end = (t + 1 < nseg) ? S.start[t + 1] : two_pi;
+    const double L = end - S.start[t];
+    S.len[t] = L > 0.0 ? L : 0.0;
+  }
+}
+
+// Mortar cells of a general interface from the segment table: m = layer *
+// (n_R + n_Rs) + segment; Gauss rule mapped into the segment, point on the
+// exact circle, face coordinates linear in the angle on each side.
+template <int K>
+__global__ void k_mortar_map_general(MortarMap A, SegTable S, int n_Rs) {
+  constexpr int N = K + 1;
+  const int nseg = A.n_R + n_Rs;
+  const int64_t M = (int64_t)A.n_z * nseg;
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int t = (int)(m % nseg);
+  const int lz = (int)(m / nseg);
+  const double Dr = 2.0 * M_PI / A.n_R, Ds = 2.0 * M_PI / n_Rs;
+  const int jr = S.jr[t], js = S.js[t];
+  const double st = S.start[t], L = S.len[t], rs = S.rstart[t], ss = js * Ds;
+  const MfTab<double>& tb = c_tab64[K];
+  A.mc_cell[2 * m] = A.ifr[(int64_t)lz * A.n_R + jr];
+  A.mc_cell[2 * m + 1] = A.ifs[(int64_t)lz * n_Rs + js];
+  A.mc_tau[m] = fmax(A.tau_r[(int64_t)lz * A.n_R + jr], A.tau_s[(int64_t)lz * n_Rs + js]);
+#pragma unroll
+  for (int g = 0; g < N; ++g) {
+    const double phi = st + tb.s[g] * L;
+    A.mc_xi[(m * 2 + 0) * N + g] = (phi - rs) / Dr;
+    A.mc_xi[(m * 2 + 1) * N + g] = (phi - ss) / Ds;
+    const double ang = A.phi0 + phi;
+    A.mc_cs[(m * N + g) * 2 + 0] = cos(ang);
+    A.mc_cs[(m * N + g) * 2 + 1] = sin(ang);
+    A.mc_w[m * N + g] = tb.w[g] * A.R * L;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Penalty tau_k = F (k+1)^2 (A(other faces)/2 + A(interface face)) / V of each
 // interface cell (Eq. EqPenalty; all non-interface faces halved).  Face areas
 // and the volume by the (k+1)-point Gauss rule on the isoparametric map.

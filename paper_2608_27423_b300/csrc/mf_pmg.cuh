@@ -19,7 +19,19 @@ namespace mf {
 struct XferTab {
   double icf[3][MF_NMAX][MF_NMAX];   // [code][fine node a][coarse node b]
   double ifc[3][MF_NMAX][MF_NMAX];   // [code][coarse node b][fine node a]
+  float icf32[3][MF_NMAX][MF_NMAX];  // FP32 copies (FP32 transfers multiply their weights in FP32)
+  float ifc32[3][MF_NMAX][MF_NMAX];
   unsigned char in_child[3][MF_NMAX];  // coarse node b lies in the child's half (code 1, 2) or always (code 0)
+};
+
+template <typename T> struct XferW;
+template <> struct XferW<double> {
+  __device__ static double icf(const XferTab& t, int c, int a, int b) { return t.icf[c][a][b]; }
+  __device__ static double ifc(const XferTab& t, int c, int b, int a) { return t.ifc[c][b][a]; }
+};
+template <> struct XferW<float> {
+  __device__ static float icf(const XferTab& t, int c, int a, int b) { return t.icf32[c][a][b]; }
+  __device__ static float ifc(const XferTab& t, int c, int b, int a) { return t.ifc32[c][b][a]; }
 };
 
 template <int D, int KF, int KC, int NFLD, int MODE, typename T>
@@ -68,15 +80,15 @@ __global__ void k_transfer(const int32_t* __restrict__ cells_f, const int32_t* _
     for (int f = 0; f < NFLD; ++f) acc[f] = T(0);
     for (int i = 0; i < NIN; ++i) {
       const int ii[3] = {i % nin, (i / nin) % nin, i / (nin * nin)};
-      double w = 1.0;
+      T w = T(1);                       // weights in the transfer's own precision
 #pragma unroll
       for (int r = 0; r < D; ++r) {
-        if (MODE == 0) w *= tb.ifc[code[r]][oi[r]][ii[r]];
-        else if (MODE == 1) w *= tb.icf[code[r]][oi[r]][ii[r]];
-        else w *= tb.icf[code[r]][ii[r]][oi[r]];
+        if (MODE == 0) w *= XferW<T>::ifc(tb, code[r], oi[r], ii[r]);
+        else if (MODE == 1) w *= XferW<T>::icf(tb, code[r], oi[r], ii[r]);
+        else w *= XferW<T>::icf(tb, code[r], ii[r], oi[r]);
       }
 #pragma unroll
-      for (int f = 0; f < NFLD; ++f) acc[f] = fma((T)w, s_in[cl][i][f], acc[f]);
+      for (int f = 0; f < NFLD; ++f) acc[f] = fma(w, s_in[cl][i][f], acc[f]);
     }
     int id = (MODE == 1) ? cells_f[cell * NPF + o] : cells_c[pcell * NPC + o];
     id = id < 0 ? ~id : id;

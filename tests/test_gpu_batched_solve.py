@@ -117,8 +117,34 @@ def test_batched_solve_iteration_cap_reports_not_converged(cases):
         ops.append(g)
         ups.append(T(u0))
     batch = BatchedOperators(ops)
-    o = solver_defaults(pc=MF_PC_JACOBI, pc_precision=MF_FP64, newton_rtol=1e-14, max_newton=2)
+    o = solver_defaults(pc=MF_PC_JACOBI, pc_precision=MF_FP64, newton_rtol=1e-14, max_newton=2, batch_fallback=0)
     st, reps = batch.solve_step(ups, [c[1]["theta"] for c in cases[:2]], o, krylov_iters=4)
     assert st == 6
     for r in reps:
         assert r.newton_iters == 2 and r.status == 6 and r.res_norm[2] < r.res_norm[0]
+        assert r.fallback_newton_iters == 0
+
+
+def test_batched_solve_fallback_finishes_instances(cases):
+    """An iteration cap that stops the batched steps above tolerance: with the
+    adaptive fallback (the default) every instance continues alone with
+    mf_solve_step from its last iterate and reaches the tolerance relative to
+    its initial residual; the report counts both parts."""
+    from paper_2608_27423_b300 import RotorStatorOperator, BatchedOperators, solver_defaults, MF_PC_JACOBI, MF_FP64
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    ops, ups = [], []
+    for mesh, prm, f, u0, _, _ in cases[:2]:
+        g = RotorStatorOperator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"])
+        g.set_history(T(f["u_n"]), T(f["u_nm1"]))
+        ops.append(g)
+        ups.append(T(u0))
+    batch = BatchedOperators(ops)
+    tol = 1e-9
+    o = solver_defaults(pc=MF_PC_JACOBI, pc_precision=MF_FP64, newton_rtol=tol, max_newton=2, restart=80,
+                        lin_rtol=1e-6, max_lin_iters=2000)
+    st, reps = batch.solve_step(ups, [c[1]["theta"] for c in cases[:2]], o, krylov_iters=4)
+    assert st == 0, [r.status for r in reps]
+    for r in reps:
+        k = r.newton_iters
+        assert r.status == 0 and r.fallback_newton_iters >= 1 and k == 2 + r.fallback_newton_iters
+        assert r.res_norm[k] <= tol * r.res_norm[0] * (1 + 1e-12)

@@ -65,8 +65,8 @@ def test_fullsize_sampled_rows(name):
     y32 = torch.empty_like(x, dtype=torch.float32)
     g.apply_jacobian(x.float(), y32, prec=MF_FP32)
     y32l = None
-    if mesh.d == 3 and mesh.k <= 3:                 # the one-cell-per-lane FP32 kernel as well
-        g.set_cells_per_block(MF_FP32, 32)
+    if mesh.d == 3 and mesh.k <= 3:                 # default: one cell per lane; also the per-point kernel
+        g.set_cells_per_block(MF_FP32, 9 if mesh.k == 2 else 4)
         y32l = torch.empty_like(x, dtype=torch.float32)
         g.apply_jacobian(x.float(), y32l, prec=MF_FP32)
         g.set_cells_per_block(MF_FP32, 0)

@@ -87,8 +87,9 @@ def test_jacobian_fp32_matches_oracle(c):
 
 @pytest.mark.parametrize("c", [c for c in CASES if c["d"] == 3], ids=cid)
 def test_jacobian_fp32_lane_kernel_matches_oracle(c):
-    """The one-cell-per-lane FP32 kernel (3D, k <= 3; FP32 variant of 32 cells
-    per block), ragged last block included."""
+    """The one-cell-per-lane FP32 kernel (3D, k <= 3; 32 cells per block,
+    ragged last block included).  On these small meshes the default FP32
+    variant is the per-point kernel (test_jacobian_fp32_matches_oracle)."""
     mesh, prm, f, op, g, T = setup(**c)
     from paper_2608_27423_b300 import MF_FP32
     g.set_cells_per_block(MF_FP32, 32)

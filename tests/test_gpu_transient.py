@@ -188,3 +188,28 @@ def test_checkpoint_resume_continues_the_run(tmp_path):
     dv = np.linalg.norm(got[:, :3] - ref[:, :3]) / np.linalg.norm(ref[:, :3])
     pa, pb = got[:, 3] - got[:, 3].mean(), ref[:, 3] - ref[:, 3].mean()
     assert dv < 1e-6 and np.linalg.norm(pa - pb) / np.linalg.norm(pb) < 1e-5, dv
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_transient_convergence_control(use_graph):
+    """step_rtol > 0: a step that the fixed budget (1 Newton iteration x
+    FGMRES(4)) leaves above step_rtol ||R_0|| gets more iterations, one graph-
+    replayed iteration at a time, until it meets the tolerance or reaches
+    max_newton; the records count the iterations.  The same run with a fixed
+    budget leaves the steps above the tolerance."""
+    from paper_2608_27423_b300 import solver_defaults, MF_PC_GMRES, MF_FP32
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    tol = 1e-7
+    ops, mesh, u0, um1 = _spin_case(1)
+    un, unm1 = T(u0), T(um1)
+    o = solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=30, step_rtol=tol, max_newton=12)
+    rec = ops[0].run_transient(un, unm1, 4, 0.137, newton_iters=1, krylov_iters=4, opts=o, use_graph=use_graph)
+    its, red = rec["newton_iters"], rec["residual_reduction"]
+    assert its[0] == 0 and np.all(its[1:] >= 1) and np.all(its[1:] <= 12), its
+    assert np.all((red[1:] <= tol) | (its[1:] == 12)), (red, its)
+    assert np.any(its[1:] > 1), its                      # the control did add iterations
+    ops, mesh, u0, um1 = _spin_case(1)
+    fixed = ops[0].run_transient(T(u0), T(um1), 4, 0.137, newton_iters=1, krylov_iters=4,
+                                 opts=solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=30),
+                                 use_graph=use_graph)
+    assert np.all(fixed["newton_iters"][1:] == 1) and np.all(fixed["residual_reduction"][1:] > tol), fixed

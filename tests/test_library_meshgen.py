@@ -103,5 +103,3 @@ def test_generator_unequal_partitions_match_input_generator(p):
     for key in ("cells", "cell_side", "node_side", "wall", "iface_rotor", "iface_stator"):
         assert np.array_equal(getattr(got, key), getattr(ref, key)), key
     assert np.abs(got.x0 - ref.x0).max() < 1e-14
-    with pytest.raises(MfError):
-        RotorStatorOperator(got, 0.01, 1.0, 0.01, 1)
