@@ -195,7 +195,7 @@ def solve_leg(args, op, mesh, prm, f, T, workload=None):
     smoothing), with the V-cycle's operator applies in FP32 (mixed) or FP64.
     Initial guess: u^n with p = 0 and zero wall velocity."""
     import torch
-    from paper_2608_27423_b300 import MF_PC_MG, MF_FP32, MF_FP64, solver_defaults
+    from paper_2608_27423_b300 import MF_PC_MG, MF_FP32, MF_FP64, solver_defaults, MF_SMOOTH_ASM, MF_SMOOTH_JACOBI
     from synth.configs import CONFIGS
     d = mesh.d
     cfg = CONFIGS[workload or args.workload]
@@ -208,14 +208,16 @@ def solve_leg(args, op, mesh, prm, f, T, workload=None):
     sols = {}
     from paper_2608_27423_b300 import MF_DF64
     wanted = set(args.solve_variants.split(","))
-    for name, pcp, outer in (("mixed_fp32_mg", MF_FP32, MF_FP64), ("fp64_mg", MF_FP64, MF_FP64),
-                             ("mixed_fp32_mg_df64_outer", MF_FP32, MF_DF64)):
+    for name, pcp, outer, smoother in (("mixed_fp32_mg", MF_FP32, MF_FP64, MF_SMOOTH_JACOBI),
+                                       ("fp64_mg", MF_FP64, MF_FP64, MF_SMOOTH_JACOBI),
+                                       ("mixed_fp32_mg_df64_outer", MF_FP32, MF_DF64, MF_SMOOTH_JACOBI),
+                                       ("mixed_fp32_mg_asm", MF_FP32, MF_FP64, MF_SMOOTH_ASM)):
         if name not in wanted:
             continue
         up = U0.clone()
         o = solver_defaults(theta=prm["theta"], pc=MF_PC_MG, pc_precision=pcp, newton_rtol=1e-8,
                             max_newton=args.max_newton, lin_rtol=1e-2, restart=30, max_lin_iters=150,
-                            mg_smooth=4, mg_coarse_iters=40, outer_precision=outer)
+                            mg_smooth=4, mg_coarse_iters=40, outer_precision=outer, mg_smoother=smoother)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, rep = op.solve_step(up, o)
@@ -223,7 +225,7 @@ def solve_leg(args, op, mesh, prm, f, T, workload=None):
         dt_s = time.perf_counter() - t0
         n_it = rep.newton_iters
         res[name] = {"status": int(st), "seconds": round(dt_s, 4), "newton_iters": n_it,
-                     "lin_iters": list(rep.lin_iters[:n_it]),
+                     "lin_iters": list(rep.lin_iters[:n_it]), "fgmres_iters": int(rep.lin_iters_total),
                      "res_reduction": (rep.res_norm[n_it] / rep.res_norm[0]) if rep.res_norm[0] > 0 else None}
         print(f"solve {name}: status {st} {dt_s:.2f}s newton {n_it} "
               f"res {rep.res_norm[0]:.3e} -> {rep.res_norm[n_it]:.3e}", file=sys.stderr, flush=True)

@@ -327,6 +327,34 @@ mf_status mf_diagonal(mf_handle h, void* diag_out, mf_precision prec, void* stre
  * each applied with pc_precision operator applies (MF_FP32: the FP32 cache). */
 typedef enum { MF_PC_JACOBI = 0, MF_PC_CHEBYSHEV = 1, MF_PC_GMRES = 2, MF_PC_MG = 3 } mf_pc_kind;
 
+/* Smoother of the MF_PC_MG levels (Section 3.4: inverse diagonal or additive
+ * Schwarz), each as the right preconditioner of the levels' smoothing GMRES:
+ *   MF_SMOOTH_JACOBI  the inverse diagonal (default);
+ *   MF_SMOOTH_ASM     additive Schwarz with cell patches: per cell the local
+ *                     matrix of Algorithm 2 (the cell's volume element matrix
+ *                     plus the own-side blocks of the mortar segments it meets,
+ *                     reconstructed column by column from the matrix-free
+ *                     kernels; wall velocity rows and columns identity),
+ *                     inverted once per linearisation in FP32; z = sum over
+ *                     cells of the local solves, each DoF's corrections averaged
+ *                     over the cells sharing it.  pc_precision must be MF_FP32.
+ *                     Levels whose local matrices exceed 108 rows (3D Q3 and
+ *                     up) keep the inverse diagonal.  Needs (d+1)^2 (k+1)^(2d)
+ *                     floats per cell on every level (6.1 GB for 131k Q2 hexes). */
+typedef enum { MF_SMOOTH_JACOBI = 0, MF_SMOOTH_ASM = 1 } mf_smoother_kind;
+
+/* mf_asm_setup: the additive Schwarz local matrices of this handle at its
+ * current linearisation (Algorithm 2, as above) and their FP32 inverses --
+ * what MF_SMOOTH_ASM does on every level inside mf_solve_step; *n_bad_pivots
+ * (host, may be NULL; synchronising when given) receives the number of pivots
+ * below 1e-30 that the inversion replaced.  mf_asm_apply: z = ASM(r) with
+ * those inverses, r and z FP32 device [n_nodes][d+1] (must not alias).
+ * Errors: MF_ERR_ARG (local matrices over 108 rows, null or aliased
+ * pointers), MF_ERR_STATE (no linearisation; apply before setup).  The first
+ * setup allocates the local matrices. */
+mf_status mf_asm_setup(mf_handle h, int* n_bad_pivots, void* stream);
+mf_status mf_asm_apply(mf_handle h, const float* r, float* z, void* stream);
+
 typedef struct {
   double newton_rtol;   /* stop when ||R||_2 <= newton_rtol ||R_0||_2 (default 1e-8) */
   double newton_atol;   /* or ||R||_2 <= newton_atol (default 0) */
@@ -354,6 +382,7 @@ typedef struct {
                              batched iterations (or stopped by the step safeguard) continues alone with
                              mf_solve_step (restart `restart`, lin_rtol, its own graphs) from its last
                              iterate, to the same absolute target newton_rtol ||R_0|| (default 1) */
+  int    mg_smoother;     /* mf_smoother_kind of MF_PC_MG (default MF_SMOOTH_JACOBI) */
   double step_rtol;       /* mf_run_transient only: > 0 turns on per-step convergence control (after
                              newton_iters iterations, one more at a time, up to max_newton per step,
                              while ||R|| > step_rtol ||R_0|| of the step); 0 = fixed iterations (default) */

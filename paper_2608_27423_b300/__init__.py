@@ -10,9 +10,10 @@ import numpy as np
 
 from . import _lib
 from ._lib import MF_FP64, MF_FP32, MF_DF64, MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG, MfError, \
+    MF_SMOOTH_JACOBI, MF_SMOOTH_ASM, \
     MfSolverOpts, MfSolveReport
 
-__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "log_open", "fma_peak", "mortar_segments", "slab_partition", "halo_pack", "halo_add", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MfError",
+__all__ = ["RotorStatorOperator", "BatchedOperators", "Mesh", "rotor_stator_mesh", "coarsen_map", "save_checkpoint", "load_checkpoint", "log_open", "fma_peak", "mortar_segments", "slab_partition", "halo_pack", "halo_add", "MF_FP64", "MF_FP32", "MF_DF64", "MF_PC_JACOBI", "MF_PC_CHEBYSHEV", "MF_PC_GMRES", "MF_PC_MG", "MF_SMOOTH_JACOBI", "MF_SMOOTH_ASM", "MfError",
            "solver_defaults"]
 
 
@@ -409,6 +410,17 @@ class RotorStatorOperator:
             out[name] = {"cells_per_block": list(r.cells_per_block[:n]), "ms": list(r.ms[:n]),
                          "chosen": r.cells_per_block[r.chosen], "from_cache": bool(r.from_cache)}
         return out
+
+    def asm_setup(self, stream=None):
+        """Additive Schwarz local matrices and FP32 inverses (mf_asm_setup);
+        returns the number of replaced pivots."""
+        bad = C.c_int()
+        self._chk(self.lib.mf_asm_setup(self.h, C.byref(bad), _stream(stream)), "mf_asm_setup")
+        return bad.value
+
+    def asm_apply(self, r, z, stream=None):
+        """z = ASM(r), FP32 device tensors (mf_asm_apply)."""
+        self._chk(self.lib.mf_asm_apply(self.h, _ptr(r), _ptr(z), _stream(stream)), "mf_asm_apply")
 
     def set_cells_per_block(self, prec, cpb):
         self._chk(self.lib.mf_set_cells_per_block(self.h, int(prec), int(cpb)), "mf_set_cells_per_block")

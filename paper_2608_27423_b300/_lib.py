@@ -13,6 +13,7 @@ STATUS_NAMES = ["MF_OK", "MF_ERR_ARG", "MF_ERR_CUDA", "MF_ERR_OOM", "MF_ERR_STAT
                 "MF_ERR_NOT_CONVERGED", "MF_ERR_BREAKDOWN", "MF_ERR_ITER_LIMIT"]
 MF_FP64, MF_FP32, MF_DF64 = 0, 1, 2
 MF_PC_JACOBI, MF_PC_CHEBYSHEV, MF_PC_GMRES, MF_PC_MG = 0, 1, 2, 3
+MF_SMOOTH_JACOBI, MF_SMOOTH_ASM = 0, 1
 
 # every symbol include/mf.h declares
 EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_mesh_params_defaults", "mf_mesh_rotor_stator", "mf_mesh_sizes",
@@ -22,7 +23,8 @@ EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_mesh_params_defaults", "mf
            "mf_profile", "mf_profile_read", "mf_mg_attach", "mf_mg_prolongate", "mf_mg_restrict",
            "mf_mg_interpolate", "mf_solve_step_static", "mf_batch_create", "mf_batch_destroy",
            "mf_batch_apply_jacobian", "mf_batch_solve_step", "mf_batch_last_error", "mf_autotune", "mf_set_cells_per_block", "mf_kinetic_energy", "mf_energy", "mf_wall_loads", "mf_run_transient", "mf_fma_peak",
-           "mf_mesh_slab", "mf_halo_pack", "mf_halo_add", "mf_mesh_from_arrays_ex"]
+           "mf_mesh_slab", "mf_halo_pack", "mf_halo_add", "mf_mesh_from_arrays_ex",
+           "mf_asm_setup", "mf_asm_apply"]
 PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
               "cell_linearization", "dirichlet", "diagonal"]
 
@@ -49,7 +51,7 @@ class MfSolverOpts(C.Structure):
                 ("cheb_lo", C.c_double), ("theta", C.c_double), ("inner_iters", C.c_int),
                 ("line_search", C.c_int), ("mg_smooth", C.c_int), ("mg_coarse_iters", C.c_int),
                 ("deflate_pressure", C.c_int), ("use_graphs", C.c_int), ("outer_precision", C.c_int),
-                ("batch_fallback", C.c_int), ("step_rtol", C.c_double)]
+                ("batch_fallback", C.c_int), ("mg_smoother", C.c_int), ("step_rtol", C.c_double)]
 
 
 class MfSolveReport(C.Structure):
@@ -154,6 +156,8 @@ def load():
     lib.mf_fma_peak.argtypes = [i32, C.POINTER(dbl), C.POINTER(dbl), vp]
     lib.mf_mesh_slab.argtypes = [vp, i32, i32, C.POINTER(vp), C.POINTER(MfSlabInfo), vp, vp, vp, vp, vp]
     lib.mf_halo_pack.argtypes = [vp, vp, i64, i32, vp, vp]
+    lib.mf_asm_setup.argtypes = [vp, C.POINTER(i32), vp]
+    lib.mf_asm_apply.argtypes = [vp, vp, vp, vp]
     lib.mf_halo_add.argtypes = [vp, vp, vp, i64, i32, vp, vp]
     for name in EXPORTS:
         f = getattr(lib, name)

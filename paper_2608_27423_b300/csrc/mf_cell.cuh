@@ -205,18 +205,26 @@ __device__ __forceinline__ void jac_point(const T (&v)[D + 1], const T (&dv)[D +
 
 // One block's worth of cells (block index `blk`) of the cell Jacobian.  The
 // tables in sm.st must be loaded and visible to the block.
-template <int D, int K, typename T, int CPB = CellCfg<D, K>::CPB>
+// ELEM = true: element-matrix columns (the volume part of the local matrix of
+// Algorithm 2): every sub-block of NQ threads works on cell `blk` with the
+// unit input vector of local DoF col = col0 + sub-block (node col / (D+1),
+// field col % (D+1); wall velocities stay zero) and writes the resulting
+// local vector to column col of E (column-major [NL][NL] per cell, NL =
+// NQ (D+1)) instead of scattering it.
+template <int D, int K, typename T, int CPB = CellCfg<D, K>::CPB, bool ELEM = false>
 __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_t blk, const int32_t* __restrict__ cells,
                                                int64_t nc, const T* __restrict__ cache,
                                                const typename IO<T>::type* __restrict__ src,
-                                               typename IO<T>::type* __restrict__ dst, T nu, T a0dt) {
+                                               typename IO<T>::type* __restrict__ dst, T nu, T a0dt,
+                                               int col0 = 0, T* __restrict__ E = nullptr) {
   using C = CellCfg<D, K>;
-  constexpr int N = C::N, NQ = C::NQ, NF = D + 1;
+  constexpr int N = C::N, NQ = C::NQ, NF = D + 1, NL = NQ * (D + 1);
   using CF = Cache<D>;
   SmTab<N, T>& st = sm.st;
   const int cl = threadIdx.x / NQ, t = threadIdx.x % NQ;
-  const int64_t cell = blk * CPB + cl;
-  const bool active = cell < nc;
+  const int64_t cell = ELEM ? blk : blk * CPB + cl;
+  const int col = col0 + cl;
+  const bool active = ELEM ? (col < NL && cell < nc) : cell < nc;
   T* tile = sm.tile[cl];
   int ii[3] = {t % N, (t / N) % N, t / (N * N)};
   const int strd[3] = {1, N, N * N};
@@ -244,7 +252,8 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_
     const bool wall = id < 0;
     node = wall ? ~id : id;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) v[f] = from_io<T>(src[(int64_t)node * NF + f]);
+    for (int f = 0; f < NF; ++f)
+      v[f] = ELEM ? T(t * NF + f == col ? 1 : 0) : from_io<T>(src[(int64_t)node * NF + f]);
     if (wall) {
 #pragma unroll
       for (int c = 0; c < D; ++c) v[c] = T(0);
@@ -361,8 +370,13 @@ __device__ __forceinline__ void cell_jac_block(JacSmem<D, K, T, CPB>& sm, int64_
     __syncthreads();
   }
   if (active) {
+    if constexpr (ELEM) {
 #pragma unroll
-    for (int f = 0; f < NF; ++f) atomic_add(&dst[(int64_t)node * NF + f], fv[f]);
+      for (int f = 0; f < NF; ++f) E[((int64_t)cell * NL + col) * NL + t * NF + f] = fv[f];
+    } else {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) atomic_add(&dst[(int64_t)node * NF + f], fv[f]);
+    }
   }
 }
 
@@ -396,6 +410,18 @@ k_cell_jac(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__ 
   __shared__ JacSmem<D, K, T, CPB> sm;
   load_tab<K, T>(sm.st);
   cell_jac_block<D, K, T, CPB>(sm, blockIdx.x, cells, nc, cache, src, dst, nu, a0dt);
+}
+
+// Element matrices of the volume terms (FP32 local matrices of the additive
+// Schwarz smoother): block (cell, column batch), CPB columns per block.
+template <int D, int K>
+__global__ void __launch_bounds__(CellCfg<D, K>::THREADS)
+k_cell_elem(const int32_t* __restrict__ cells, int64_t nc, const float* __restrict__ cache, float nu, float a0dt,
+            float* __restrict__ E) {
+  __shared__ JacSmem<D, K, float> sm;
+  load_tab<K, float>(sm.st);
+  cell_jac_block<D, K, float, CellCfg<D, K>::CPB, true>(sm, blockIdx.x, cells, nc, cache, nullptr, nullptr, nu, a0dt,
+                                                       blockIdx.y * CellCfg<D, K>::CPB, E);
 }
 
 // ---------------------------------------------------------------------------

@@ -126,6 +126,10 @@ struct mf_ctx {
   double* react = nullptr;             // reaction rows scratch of mf_wall_loads [n_dofs]
   double* cache64 = nullptr;
   float* cache32 = nullptr;
+  float* asm_E = nullptr;              // additive Schwarz: inverted local matrices [nc][NL][NL] (FP32)
+  int* asm_bad = nullptr;              // pivots replaced during the last inversion
+  float* inv_mult32 = nullptr;         // 1 / (cells sharing the node)
+  bool asm_on = false;                 // the level's smoother uses the local inverses
   float* lcache32 = nullptr;           // 3D, k <= 3: FP32 cache in the lane layout (k_cell_jac_lane)
   int32_t* lcells = nullptr;           // 3D, k <= 3: lane-interleaved cell table
   Workspace ws;
@@ -428,7 +432,7 @@ extern "C" mf_status mf_destroy(mf_handle h) {
   void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
                   h->mc_cell, h->mc_tau, h->mc_xi, h->mc_cs, h->mc_w, h->ht, h->g, h->cache64, h->cache32,
                   h->mg_jinv64, h->mg_jinv32, h->mg_jinvdf, h->cachedf, h->react, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32,
-                  h->lcache32, h->lcells, h->seg.start, h->seg.len, h->seg.rstart, h->seg.jr, h->seg.js};
+                  h->lcache32, h->lcells, h->asm_E, h->asm_bad, h->inv_mult32, h->seg.start, h->seg.len, h->seg.rstart, h->seg.jr, h->seg.js};
   for (void* p : ptrs) if (p) cudaFree(p);
   free_ws(h->ws);
   delete h;
@@ -736,6 +740,7 @@ extern "C" mf_status mf_profile_read(mf_handle h, mf_profile_t* out) {
   return MF_OK;
 }
 
+#include "mf_asm.inc"
 #include "mf_solve.inc"
 #include "mf_mg.inc"
 #include "mf_transient.inc"

@@ -503,15 +503,26 @@ template <int D, int K, typename T> struct MortarApplySmem {
   T dL1[MPB][2][N][N];
 };
 
-template <int D, int K, typename T>
-__device__ __forceinline__ void mortar_apply_block(MortarApplySmem<D, K, T>& S, int64_t blk, const MortarArgs<T>& A) {
+// ELEM = true (Algorithm 2, mortar part of the local matrices): slot lm of
+// the block is (mortar cell mc, column side sc, local DoF column j), slot =
+// blk * MPB + lm = (mc * 2 + sc) * NL + j; the input is the unit vector of DoF
+// j on side sc (zero on the other side, wall velocities zero) and side sc's
+// rows of the result, the own-side block's column j, are added to E[cell]
+// (column-major [NL][NL]); the other side's rows (the coupling block) belong
+// to no local matrix and are dropped.
+template <int D, int K, typename T, bool ELEM = false>
+__device__ __forceinline__ void mortar_apply_block(MortarApplySmem<D, K, T>& S, int64_t blk, const MortarArgs<T>& A,
+                                                   T* __restrict__ E = nullptr) {
   using C = MortarCfg<D, K>;
   using SM = MortarApplySmem<D, K, T>;
-  constexpr int N = C::N, NPC = C::NPC, NP = C::NP, NF = D + 1, TPM = 2 * NPC;
+  constexpr int N = C::N, NPC = C::NPC, NP = C::NP, NF = D + 1, TPM = 2 * NPC, NL = NPC * NF;
   const MfTab<T>& tb = TabSel<T>::get(K);
   const int lm = threadIdx.x / TPM;
   const int loc = threadIdx.x % TPM;
-  const int64_t mc = blk * C::MPB + lm;
+  const int64_t slot = blk * C::MPB + lm;
+  const int64_t mc = ELEM ? slot / (2 * NL) : slot;
+  const int sc = ELEM ? (int)((slot / NL) % 2) : 0;
+  const int jcol = ELEM ? (int)(slot % NL) : 0;
   const bool active = mc < A.nm;
   // region views, per side
   auto val = [&](int s, int a, int f) -> T& { return S.r1[lm][s][a * NF + f]; };
@@ -539,8 +550,9 @@ __device__ __forceinline__ void mortar_apply_block(MortarApplySmem<D, K, T>& S, 
       const bool wall = id < 0;
       node = wall ? ~id : id;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) val(s, a, f) = from_io<T>(A.src[(int64_t)node * NF + f]);
-      if (wall && A.zero_wall) {
+      for (int f = 0; f < NF; ++f)
+        val(s, a, f) = ELEM ? T(s == sc && a * NF + f == jcol ? 1 : 0) : from_io<T>(A.src[(int64_t)node * NF + f]);
+      if (wall && (ELEM || A.zero_wall)) {
 #pragma unroll
         for (int c = 0; c < D; ++c) val(s, a, c) = T(0);
       }
@@ -734,9 +746,24 @@ __device__ __forceinline__ void mortar_apply_block(MortarApplySmem<D, K, T>& S, 
 #pragma unroll
     for (int c = 0; c < D; ++c) out[c] = (a0 == fc) ? fma(dl, H(s, q, c), G(s, q, c)) : dl * H(s, q, c);
     out[D] = (a0 == fc) ? G(s, q, D) : T(0);
+    if constexpr (ELEM) {
+      if (s == sc) {
+        T* col = E + ((int64_t)A.mc_cell[2 * mc + s] * NL + jcol) * NL + a * NF;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) atomic_add(&A.dst[(int64_t)node * NF + f], out[f]);
+        for (int f = 0; f < NF; ++f) atomicAdd(col + f, out[f]);
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) atomic_add(&A.dst[(int64_t)node * NF + f], out[f]);
+    }
   }
+}
+
+// Mortar own-side blocks of the local matrices (FP32): nm * 2 * NL slots.
+template <int D, int K>
+__global__ void __launch_bounds__(MortarCfg<D, K>::THREADS) k_mortar_elem(MortarArgs<float> A, float* __restrict__ E) {
+  __shared__ MortarApplySmem<D, K, float> S;
+  mortar_apply_block<D, K, float, true>(S, blockIdx.x, A, E);
 }
 
 template <int D, int K, typename T, int MODE>

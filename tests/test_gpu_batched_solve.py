@@ -130,7 +130,7 @@ def test_batched_solve_fallback_finishes_instances(cases):
     adaptive fallback (the default) every instance continues alone with
     mf_solve_step from its last iterate and reaches the tolerance relative to
     its initial residual; the report counts both parts."""
-    from paper_2608_27423_b300 import RotorStatorOperator, BatchedOperators, solver_defaults, MF_PC_JACOBI, MF_FP64
+    from paper_2608_27423_b300 import RotorStatorOperator, BatchedOperators, solver_defaults, MF_PC_GMRES, MF_FP32
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     ops, ups = [], []
     for mesh, prm, f, u0, _, _ in cases[:2]:
@@ -140,8 +140,8 @@ def test_batched_solve_fallback_finishes_instances(cases):
         ups.append(T(u0))
     batch = BatchedOperators(ops)
     tol = 1e-9
-    o = solver_defaults(pc=MF_PC_JACOBI, pc_precision=MF_FP64, newton_rtol=tol, max_newton=2, restart=80,
-                        lin_rtol=1e-6, max_lin_iters=2000)
+    o = solver_defaults(pc=MF_PC_GMRES, pc_precision=MF_FP32, inner_iters=40, newton_rtol=tol, max_newton=2,
+                        restart=30, lin_rtol=1e-6, max_lin_iters=300)
     st, reps = batch.solve_step(ups, [c[1]["theta"] for c in cases[:2]], o, krylov_iters=4)
     assert st == 0, [r.status for r in reps]
     for r in reps:
