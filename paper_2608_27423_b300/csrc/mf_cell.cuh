@@ -465,7 +465,9 @@ k_cell_jac_batched(const BatchTable<T>* __restrict__ tab, unsigned long long* __
 // State evaluation at Gauss points (FP64).  MODE 0: write the linearisation
 // cache at the state up (Section 2.3 Jacobian coefficients).  MODE 1: residual
 // volume terms of Eq. Eq-NSweakComplete (with the integrated-by-parts pressure
-// and viscous terms of Eq. Eq-NSweakWmortar), dst += R_cell(up).
+// and viscous terms of Eq. Eq-NSweakWmortar), dst += R_cell(up).  MODE 2:
+// both in one pass (a Newton step needs the residual and the linearisation at
+// the same state; they share the interpolation, geometry and tau).
 struct StateArgs {
   const int32_t* cells; int64_t nc;
   const double* x;          // [N_n][D] current coordinates
@@ -477,8 +479,11 @@ struct StateArgs {
   double nu, omega, a0dt, inv_dt2;
 };
 
+#ifndef MF_STATE_MINB
+#define MF_STATE_MINB 1      // resident blocks of the FP64 state kernel requested from the register allocator
+#endif
 template <int D, int K, int MODE>
-__global__ void __launch_bounds__(CellCfg<D, K>::THREADS) k_cell_state(StateArgs A) {
+__global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MF_STATE_MINB) k_cell_state(StateArgs A) {
   using C = CellCfg<D, K>;
   using T = double;
   constexpr int N = C::N, NQ = C::NQ, NF = D + 1;
@@ -678,7 +683,7 @@ __global__ void __launch_bounds__(CellCfg<D, K>::THREADS) k_cell_state(StateArgs
     Rs[c] = A.a0dt * U[c] + v[2 * D + 1 + c] + cv + gP[c] - A.nu * lU[c];
   }
 
-  if (MODE == 0) {
+  if (MODE == 0 || MODE == 2) {
     if (active) {
       const int64_t Pn = A.nc * NQ;
       double* cp = A.cache + cell * NQ + t;
@@ -701,6 +706,8 @@ __global__ void __launch_bounds__(CellCfg<D, K>::THREADS) k_cell_state(StateArgs
       for (int c = 0; c < D; ++c) cp[(CF::RS + c) * Pn] = Rs[c];
       cp[CF::TAU * Pn] = tau;
     }
+  }
+  if (MODE == 0) {
     return;
   } else {
     // residual fluxes

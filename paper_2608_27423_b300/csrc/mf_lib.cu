@@ -221,7 +221,8 @@ static void launch_state(mf_ctx* h, int mode, const double* up, double* dst, cud
   const unsigned g = nblk(h->nc, C::CPB);
   ProfScope ps(h, mode == 0 ? 5 : 4, st);
   if (mode == 0) k_cell_state<D, K, 0><<<g, C::THREADS, 0, st>>>(A);
-  else k_cell_state<D, K, 1><<<g, C::THREADS, 0, st>>>(A);
+  else if (mode == 1) k_cell_state<D, K, 1><<<g, C::THREADS, 0, st>>>(A);
+  else k_cell_state<D, K, 2><<<g, C::THREADS, 0, st>>>(A);
 }
 
 // The one-cell-per-lane FP32 kernel (mf_lane.cuh) exists for 3D, k = 1..3;
@@ -593,6 +594,24 @@ extern "C" mf_status mf_set_linearization(mf_handle h, const double* up_star, do
   h->have_lin = true;
   h->df_valid = false;
   return MF_OK;
+}
+
+// Residual r = F-hat*_NS(up) (as mf_residual) and, from the same pass over the
+// cells, the linearisation cache at up (as mf_set_linearization at the
+// handle's current angle): the Newton loop needs both at every new iterate.
+static mf_status residual_rows(mf_ctx* h, const double* up, double* r, cudaStream_t st);
+static mf_status residual_constrain(mf_ctx* h, const double* up, double* r, cudaStream_t st);
+static mf_status residual_and_linearize(mf_ctx* h, const double* up, double* r, cudaStream_t st) {
+  CK(cudaMemsetAsync(r, 0, h->ndof * 8, st));
+  MF_DISPATCH(h->d, h->k, (launch_state<D, K>(h, 2, up, r, st)));
+  MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, double>(h, 0, up, r, 0, st)));
+  const int64_t ncv = (int64_t)h->ncache * h->nc * ipow(h->k + 1, h->d);
+  k_cast<double, float><<<nblk(ncv, 256), 256, 0, st>>>(h->cache64, h->cache32, ncv);
+  if (h->lcache32) MF_DISPATCH(h->d, h->k, (launch_lane_cache<D, K>(h, st)));
+  CK(cudaGetLastError());
+  h->have_lin = true;
+  h->df_valid = false;
+  return residual_constrain(h, up, r, st);
 }
 
 // Volume + mortar residual rows without the Dirichlet replacement (on wall

@@ -254,9 +254,14 @@ __global__ void k_mdot_final(const double* __restrict__ part, int nb, double* __
 template <typename T>
 __global__ void k_maxpy(int64_t n, int m, const T* __restrict__ V, int64_t ldv, const double* __restrict__ h,
                         double sign, T* __restrict__ w) {
+  // the m coefficients, scaled and rounded to T once per block (m <= 256:
+  // restart lengths and inner dimensions are capped below that)
+  __shared__ T c[256];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) c[i] = (T)(sign * h[i]);
+  __syncthreads();
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     T s = w[j];
-    for (int i = 0; i < m; ++i) s = fma((T)(sign * __ldg(h + i)), V[(int64_t)i * ldv + j], s);
+    for (int i = 0; i < m; ++i) s = fma(c[i], V[(int64_t)i * ldv + j], s);
     w[j] = s;
   }
 }
