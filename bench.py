@@ -62,10 +62,13 @@ def parse():
     ap.add_argument("--clocks-dir", default=None, help="where the nvidia-smi clock samples are written (default: temp)")
     ap.add_argument("--solve-only", action="store_true",
                     help="profiling aid: run only the Newton-step leg on --workload and print its JSON")
+    ap.add_argument("--solve-cold", action="store_true",
+                    help="time each solve variant's first call (workspace allocation and graph capture included)")
     ap.add_argument("--solve-variants", default="mixed_fp32_mg,fp64_mg,mixed_fp32_mg_df64_outer",
                     help="comma list of the solve leg's variants")
     ap.add_argument("--q3-workload", default="3d_q3", help="the Q3 workload of the q3 leg")
     ap.add_argument("--no-q3", action="store_true", help="skip the Q3 leg")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core interpolation probe")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default cells per block (profiling runs: timings under ncu are not representative)")
     return ap.parse_args()
@@ -214,17 +217,28 @@ def solve_leg(args, op, mesh, prm, f, T, workload=None):
                                        ("mixed_fp32_mg_asm", MF_FP32, MF_FP64, MF_SMOOTH_ASM)):
         if name not in wanted:
             continue
-        up = U0.clone()
         o = solver_defaults(theta=prm["theta"], pc=MF_PC_MG, pc_precision=pcp, newton_rtol=1e-8,
                             max_newton=args.max_newton, lin_rtol=1e-2, restart=30, max_lin_iters=150,
                             mg_smooth=4, mg_coarse_iters=40, outer_precision=outer, mg_smoother=smoother)
+        # the first solve of a variant also allocates its workspaces and
+        # captures its V-cycle graph; the timed one is the next, from the
+        # same initial guess (as every later time step would run)
+        first = None
+        if not args.solve_cold:
+            up = U0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            op.solve_step(up, o)
+            torch.cuda.synchronize()
+            first = round(time.perf_counter() - t0, 4)
+        up = U0.clone()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         st, rep = op.solve_step(up, o)
         torch.cuda.synchronize()
         dt_s = time.perf_counter() - t0
         n_it = rep.newton_iters
-        res[name] = {"status": int(st), "seconds": round(dt_s, 4), "newton_iters": n_it,
+        res[name] = {"status": int(st), "seconds": round(dt_s, 4), "first_solve_seconds": first, "newton_iters": n_it,
                      "lin_iters": list(rep.lin_iters[:n_it]), "fgmres_iters": int(rep.lin_iters_total),
                      "res_reduction": (rep.res_norm[n_it] / rep.res_norm[0]) if rep.res_norm[0] > 0 else None}
         print(f"solve {name}: status {st} {dt_s:.2f}s newton {n_it} "
@@ -405,6 +419,7 @@ def batched_leg(args, T, dev):
         its = [r.newton_iters for r in reps]
         out[f"solve_{label}"] = {"status": int(st), "seconds": round(dt_s, 4), "fgmres_per_newton": 8,
                                  "newton_iters": its, "statuses": [int(r.status) for r in reps],
+                                 "fallback_newton_iters": [int(r.fallback_newton_iters) for r in reps],
                                  "res_reduction": [float(r.res_norm[r.newton_iters] / r.res_norm[0]) for r in reps]}
         print(f"batched solve {label}: status {st} {dt_s:.2f}s newton {its} statuses "
               f"{[int(r.status) for r in reps]}", file=sys.stderr, flush=True)
@@ -413,6 +428,59 @@ def batched_leg(args, T, dev):
     out["solve_rel_diff_batched_vs_one_by_one"] = [float((a[:, :3] - b[:, :3]).norm() / b[:, :3].norm())
                                                    for a, b in zip(sols["batched"], sols["one_by_one"])]
     return out
+
+
+# --------------------------------------------------------------------- end to end
+def e2e_pipelined(op, x, steps, stream):
+    """Milliseconds for `steps` end-to-end applies through the public API:
+    step i copies its input from pinned host memory (two host / device
+    buffers used in turn), applies the Jacobian and copies the result back;
+    the host-to-device copy of step i+1 and the device-to-host copy of step
+    i-1 run on their own streams while step i computes.  Timed with CUDA
+    events from before the first copy to after the last result is on the
+    host."""
+    import torch
+    xh = [torch.empty(x.shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    yh = [torch.empty(x.shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    for b in xh:
+        b.copy_(x.cpu())
+    xd = [torch.empty_like(x) for _ in range(2)]
+    yd = [torch.empty_like(x) for _ in range(2)]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()
+    applied = [ev(), ev()]
+    copied_in = [ev(), ev()]
+    copied_out = [ev(), ev()]
+
+    def run(n):
+        used = [False, False]
+        for i in range(n):
+            b = i % 2
+            if used[b]:
+                s_in.wait_event(applied[b])
+            with torch.cuda.stream(s_in):
+                xd[b].copy_(xh[b], non_blocking=True)
+            copied_in[b].record(s_in)
+            stream.wait_event(copied_in[b])
+            if used[b]:
+                stream.wait_event(copied_out[b])
+            op.apply_jacobian(xd[b], yd[b], stream=stream)
+            applied[b].record(stream)
+            s_out.wait_event(applied[b])
+            with torch.cuda.stream(s_out):
+                yh[b].copy_(yd[b], non_blocking=True)
+            copied_out[b].record(s_out)
+            used[b] = True
+        stream.wait_stream(s_out)
+    run(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s_in.wait_stream(stream)
+    run(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
 
 
 # --------------------------------------------------------------------- Q3 leg
@@ -474,6 +542,49 @@ def peaks_leg(clocks_path, local):
             "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS, "clocks": clocks,
             "how": "mf_fma_peak: 8 independent FMA chains per thread, 2048 threads per SM on every SM, "
                    "2 warm-up + 5 timed launches (CUDA events)"}
+
+
+# --------------------------------------------------------------------- tensor-core measurement
+def tc_leg(args):
+    """Interpolation stage of the Q2 cell kernel (nodal values of 4 fields ->
+    values + first derivatives at 27 Gauss points) as a compute-only probe
+    (mf_contract_probe), one tile of 32 cells per CTA on every SM, repeated:
+    FP32 FMA sum factorisation against tcgen05 TF32 and 3xTF32 dense Kronecker
+    products.  Reports cells/s, the time the stage would take for the 3d_q2
+    cylinder at that rate, and each variant's deviation from the FMA result."""
+    import torch
+    from paper_2608_27423_b300 import contract_probe
+    # the tensor-core kernel runs one CTA (4 warps) per SM; the FMA kernel gets
+    # 8 CTAs per SM (32 warps) for the same total work
+    launch = {0: (148 * 8, 512), 1: (148, 4096), 2: (148, 4096)}
+    g = torch.Generator(device="cuda").manual_seed(7)
+    u = torch.rand((148 * 8, 27, 4, 32), generator=g, device="cuda", dtype=torch.float32) * 2 - 1
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    outs = {v: torch.empty((148, 108, 4, 32), dtype=torch.float32, device="cuda") for v in (0, 1, 2)}
+    sums = torch.empty((148 * 8, 4, 32), dtype=torch.float32, device="cuda")
+    res = {"launch_blocks_reps": launch, "cells_per_tile": 32, "fields": 4, "outputs_per_field": 108}
+    names = {0: "fp32_fma_sum_factorised", 1: "tcgen05_tf32", 2: "tcgen05_3xtf32"}
+    for v in (0, 1, 2):
+        contract_probe(v, u[:148], outs[v], reps=1, err=err)
+    for v in (0, 1, 2):
+        blocks, reps = launch[v]
+        for _ in range(2):
+            contract_probe(v, u[:blocks], sums[:blocks], reps=reps, err=err)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        contract_probe(v, u[:blocks], sums[:blocks], reps=reps, err=err)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        cells = blocks * 32 * reps
+        macs = {0: 729, 1: 2916, 2: 3 * 2916}[v] * 4      # useful multiply-adds per cell (4 fields)
+        res[names[v]] = {"ms": ms, "cells_per_s": cells / (ms * 1e-3),
+                         "us_for_131072_cells": 131072 / (cells / (ms * 1e-3)) * 1e6,
+                         "useful_tflops": 2 * macs * cells / (ms * 1e-3) / 1e12,
+                         "max_rel_diff_vs_fma": float((outs[v] - outs[0]).abs().max() / outs[0].abs().max())}
+    res["tensor_core_error_flag"] = int(err.item())
+    return res
 
 
 # --------------------------------------------------------------------- CPU oracle
@@ -815,10 +926,15 @@ def main():
         xd.copy_(xh, non_blocking=True)
         op.apply_jacobian(xd, y)
         yh.copy_(y, non_blocking=True)
-    ms_e2e = timed(e2e_step, max(20, args.steps // 5), 2)
     e2e_steps = max(20, args.steps // 5)
-    e2e = {"value": n_dofs * world / (ms_e2e / e2e_steps * 1e-3), "unit": "DoFs/s",
-           "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(yh.numel() * 8)}
+    ms_e2e = timed(e2e_step, e2e_steps, 2)
+    serial = n_dofs * world / (ms_e2e / e2e_steps * 1e-3)
+    ms_pipe = e2e_pipelined(op, x, e2e_steps, stream)
+    e2e = {"value": n_dofs * world / (ms_pipe / e2e_steps * 1e-3), "unit": "DoFs/s",
+           "h2d_bytes_per_step": int(xh.numel() * 8), "d2h_bytes_per_step": int(yh.numel() * 8),
+           "mode": "every step copies its input host->device and its result device->host (pinned host buffers); "
+                   "copies run on two copy streams, overlapped with the neighbouring steps' applies",
+           "serial_value": serial}
 
     # ---- nonlinear step to 1e-8: all-FP64 vs mixed precision (same algorithm)
     # optional legs: a failure is reported in the line instead of losing the line
@@ -834,6 +950,8 @@ def main():
         op.set_linearization(up_star, prm["theta"])
     if not args.no_q3:
         leg("q3", lambda: q3_leg(args, T, timed))
+    if not args.no_tc:
+        leg("interpolation_tensor_cores", lambda: tc_leg(args))
     if args.batched:
         leg("batched_12", lambda: batched_leg(args, T, dev))
     if args.transient > 0:

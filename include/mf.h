@@ -653,6 +653,31 @@ mf_status mf_profile_read(mf_handle h, mf_profile_t* out); /* synchronising */
  * (a measurement aid: the paper reports no roofline). */
 mf_status mf_fma_peak(int prec, double* tflops, double* ms_out, void* stream);
 
+/* mf_contract_probe: the interpolation stage of the 3D Q2 cell kernel (nodal
+ * values of the four fields -> values and the three first reference
+ * derivatives at the 27 Gauss points, Section 3.1 sum factorisation) as a
+ * compute-only kernel, to measure whether these batched contractions are
+ * dense enough for the tensor cores.  Each of `blocks` CTAs loads its tile of
+ * 32 cells x 4 fields into shared memory once and contracts it `reps` times.
+ *   variant 0: FP32 FMA, sum-factorised (729 FMAs per field and cell);
+ *   variant 1: tcgen05.mma kind::tf32, the tile as one dense product
+ *              [128 rows = field x cell] x [32 = nodes, 27 used] against the
+ *              Kronecker basis [112 outputs, 108 used] (2916 MACs per field and
+ *              cell), accumulator in TMEM (double-buffered), tcgen05.ld back;
+ *   variant 2: as 1 with hi/lo TF32 splits of both operands and three
+ *              products per step (FP32-level accuracy).
+ * u   : device, [blocks][27 nodes][4 fields][32 cells] floats; node
+ *       a = ax + 3 ay + 9 az (Gauss-Lobatto nodes of mf_mesh cells).
+ * out : device; reps == 1: [blocks][108][4][32], output n = q (value at Gauss
+ *       point q = qx + 3 qy + 9 qz) or 27 (1 + d) + q (d/dxi_d there);
+ *       reps > 1: [blocks][4][32] sums of all outputs over the repetitions.
+ * err : device int (variants 1, 2), set to 1 when a wait on the tensor core
+ *       ran out (the outputs are then invalid); never cleared here.
+ * Asynchronous on `stream`; the caller times it.  MF_ERR_ARG for a bad
+ * variant, blocks < 1, reps < 1 or a null pointer.  Not in the paper (a
+ * measurement aid). */
+mf_status mf_contract_probe(int variant, int blocks, int reps, const float* u, float* out, int* err, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -224,6 +224,18 @@ def fma_peak(prec=MF_FP64, stream=None):
     return tf.value, ms.value
 
 
+def contract_probe(variant, u, out, reps=1, err=None, stream=None):
+    """Interpolation-stage probe (mf_contract_probe): variant 0 FP32 FMA sum
+    factorisation, 1 tcgen05 TF32, 2 tcgen05 3xTF32.  u: device float32
+    [blocks, 27, 4, 32]; out: device float32 [blocks, 108, 4, 32] (reps == 1)
+    or [blocks, 4, 32] (sums over reps > 1); err: device int32 [1] (variants
+    1, 2).  Asynchronous on `stream`."""
+    blocks = int(u.shape[0])
+    _check(_lib.load().mf_contract_probe(int(variant), blocks, int(reps), _ptr(u), _ptr(out),
+                                         _ptr(err) if err is not None else None, _stream(stream)),
+           None, "mf_contract_probe")
+
+
 def _host_f64(a):
     if hasattr(a, "detach"):
         a = a.detach().cpu().numpy()

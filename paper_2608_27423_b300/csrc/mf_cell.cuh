@@ -480,7 +480,7 @@ struct StateArgs {
 };
 
 #ifndef MF_STATE_MINB
-#define MF_STATE_MINB 1      // resident blocks of the FP64 state kernel requested from the register allocator
+#define MF_STATE_MINB 2      // resident blocks of the FP64 state kernel requested from the register allocator (2: 7-9 % faster than 1 at Q2/Q3)
 #endif
 template <int D, int K, int MODE>
 __global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MF_STATE_MINB) k_cell_state(StateArgs A) {

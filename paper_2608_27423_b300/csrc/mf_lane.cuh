@@ -21,6 +21,9 @@
 #pragma once
 #include "mf_cell.cuh"
 
+#ifndef MF_LANE_L2_PREFETCH
+#define MF_LANE_L2_PREFETCH 1 // bulk-prefetch the block's coefficient planes into L2 at the start
+#endif
 #ifndef MF_LANE_MINB_Q2
 #define MF_LANE_MINB_Q2 2     // Q2: two 288-thread blocks per SM (96 registers, no spills)
 #endif
@@ -104,6 +107,17 @@ k_cell_jac_lane(const int32_t* __restrict__ lcells, int64_t nc, const float* __r
   auto sp = [&](int pl, int p) -> float& { return S[(pl * NQ + p) * CB + lane]; };
   const float* lcb = lc + (int64_t)blockIdx.x * LC::NF * NQ * CB + lane;
   const int32_t* lcl = lcells + (int64_t)blockIdx.x * NQ * CB + lane;
+#if MF_LANE_L2_PREFETCH
+  // The coefficients are read only in the point phase, after the gather and
+  // four sum-factorisation sweeps; one bulk L2 prefetch per field plane
+  // (NQ x 32 floats, contiguous, 16-byte aligned: a multiple of 128 B from
+  // the allocation's start) moves their HBM traffic under those sweeps.
+  if (threadIdx.x < LC::NF) {
+    const float* plane = lc + ((int64_t)blockIdx.x * LC::NF + threadIdx.x) * NQ * CB;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(plane), "r"((unsigned)(NQ * CB * sizeof(float)))
+                 : "memory");
+  }
+#endif
 
   // ---- gather the pencil's nodal values (wall velocities as zero)
   int node[N];

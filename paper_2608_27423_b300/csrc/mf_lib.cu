@@ -135,6 +135,8 @@ struct mf_ctx {
   Workspace ws;
   MgLink mg;
   cudaStream_t cap_stream = nullptr;   // library stream for graph capture
+  cudaStream_t side = nullptr;         // high-priority stream the mortar apply runs on beside the cell kernel
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* d_theta = nullptr;           // device copy of the rotor angle (transient driver)
   bool own_theta = false;              // d_theta allocated by this handle
   bool theta_on_dev = false;           // kernels read the angle from d_theta
@@ -430,6 +432,9 @@ extern "C" mf_status mf_destroy(mf_handle h) {
   if (h->mg_exec) cudaGraphExecDestroy(h->mg_exec);
   if (h->d_theta && h->own_theta) cudaFree(h->d_theta);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   void* ptrs[] = {h->x0, h->x, h->node_side, h->cell_side, h->cells, h->wall, h->ifr, h->ifs, h->tau_r, h->tau_s,
                   h->mc_cell, h->mc_tau, h->mc_xi, h->mc_cs, h->mc_w, h->ht, h->g, h->cache64, h->cache32,
                   h->mg_jinv64, h->mg_jinv32, h->mg_jinvdf, h->cachedf, h->react, h->mg.parent, h->mg.child, h->mg.inv_mult64, h->mg.inv_mult32,
@@ -517,6 +522,12 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
       const size_t padded = (nc + 31) / 32 * 32;
       ALLOC2(h->lcells, padded * npc); ALLOC2(h->lcache32, (size_t)LaneCache::NF * padded * npc);
     }
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return fail(MF_ERR_CUDA);
   } while (0);
 #undef ALLOC2
   if (cudaMemcpy(h->x0, m->x0.data(), nn * d * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -668,14 +679,28 @@ extern "C" mf_status mf_wall_loads(mf_handle h, const double* up, const uint8_t*
   return wall_loads_from_rows(h, up, h->react, group, n_groups, out, st);
 }
 
+#ifndef MF_OVERLAP_MORTAR
+#define MF_OVERLAP_MORTAR 7   // precisions whose apply runs the mortar beside the cell kernel: 1 FP64, 2 FP32, 4 DF64
+#endif
 template <typename T>
 static mf_status apply_t(mf_ctx* h, const typename IO<T>::type* x, typename IO<T>::type* y, cudaStream_t st) {
   using TI = typename IO<T>::type;
   const T* cache = std::is_same<T, double>::value ? (const T*)h->cache64
                  : std::is_same<T, float>::value ? (const T*)h->cache32 : (const T*)h->cachedf;
   CK(cudaMemsetAsync(y, 0, h->ndof * sizeof(TI), st));
-  MF_DISPATCH(h->d, h->k, (launch_jac<D, K, T>(h, cache, x, y, st)));
-  MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 0, x, y, 1, st)));
+  if (MF_OVERLAP_MORTAR & (std::is_same<T, double>::value ? 1 : std::is_same<T, float>::value ? 2 : 4)) {
+    // Both kernels scatter with atomics into the zeroed y: the mortar blocks
+    // run on the high-priority side stream, beside the cell kernel's waves.
+    CK(cudaEventRecord(h->ev_fork, st));
+    CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 0, x, y, 1, h->side)));
+    MF_DISPATCH(h->d, h->k, (launch_jac<D, K, T>(h, cache, x, y, st)));
+    CK(cudaEventRecord(h->ev_join, h->side));
+    CK(cudaStreamWaitEvent(st, h->ev_join, 0));
+  } else {
+    MF_DISPATCH(h->d, h->k, (launch_jac<D, K, T>(h, cache, x, y, st)));
+    MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 0, x, y, 1, st)));
+  }
   if (h->nwall) {
     ProfScope ps(h, 6, st);
     if (h->d == 2) k_dirichlet_copy<2, TI><<<nblk(h->nwall, 256), 256, 0, st>>>(h->wall, h->nwall, x, y);
@@ -765,6 +790,7 @@ extern "C" mf_status mf_profile_read(mf_handle h, mf_profile_t* out) {
 #include "mf_transient.inc"
 #include "mf_autotune.inc"
 #include "mf_probe.inc"
+#include "mf_tc.inc"
 
 // ---------------------------------------------------------------- batched instances
 struct mf_batch {
