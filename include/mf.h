@@ -380,7 +380,8 @@ typedef struct {
                              (FP64-accurate double-float on the FP32 pipes) */
   int    batch_fallback;  /* mf_batch_solve_step only: 1 = an instance still above tolerance after the
                              batched iterations (or stopped by the step safeguard) continues alone with
-                             mf_solve_step (restart `restart`, lin_rtol, its own graphs) from its last
+                             mf_solve_step (restart max(restart, 30), lin_rtol, max(max_newton, 40)
+                             iterations, MG smoothing max(2 mg_smooth, 8), its own graphs) from its last
                              iterate, to the same absolute target newton_rtol ||R_0|| (default 1) */
   int    mg_smoother;     /* mf_smoother_kind of MF_PC_MG (default MF_SMOOTH_JACOBI) */
   double step_rtol;       /* mf_run_transient only: > 0 turns on per-step convergence control (after
@@ -562,8 +563,9 @@ mf_status mf_batch_apply_jacobian(mf_batch* b, const void* const* xs, void* cons
  * res_norm[0..newton_iters], lin_iters, wall seconds of the call, status.
  * With so->batch_fallback = 1 (default), an instance that has not converged
  * when the batched loop ends continues alone with mf_solve_step (adaptive
- * FGMRES(restart), same preconditioner) from its last iterate until ||R_i|| <=
- * newton_rtol ||R_i,0||; its report then covers both parts
+ * FGMRES(max(restart, 30)), the same preconditioner with twice the multigrid
+ * smoothing steps, at least 8, up to max(max_newton, 40) iterations) from its
+ * last iterate until ||R_i|| <= newton_rtol ||R_i,0||; its report then covers both parts
  * (fallback_newton_iters says how many iterations the fallback took).
  * Returns MF_OK when every instance converged, otherwise the first failing
  * instance's status (MF_ERR_NOT_CONVERGED or MF_ERR_NAN; ups then hold the

@@ -172,9 +172,10 @@ struct ProfScope {
 
 static inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
-// grid of the grid-stride vector kernels (256 threads): about 4 entries per
-// thread, at most 8 blocks per SM
-static inline unsigned vgrid(int64_t n) { return (unsigned)std::min<int64_t>(148 * 8, std::max<int64_t>(1, (n + 1023) / 1024)); }
+// grid of the grid-stride vector kernels (256 threads): one entry per thread
+// up to 8 blocks per SM (short coarse-level vectors are latency-bound: spread
+// them over as many SMs as they fill), grid-stride beyond
+static inline unsigned vgrid(int64_t n) { return (unsigned)std::min<int64_t>(148 * 8, std::max<int64_t>(1, (n + 255) / 256)); }
 
 static mf_status upload_tables(mf_ctx* h) {
   int dev = 0;

@@ -259,10 +259,21 @@ __global__ void k_maxpy(int64_t n, int m, const T* __restrict__ V, int64_t ldv, 
   __shared__ T c[256];
   for (int i = threadIdx.x; i < m; i += blockDim.x) c[i] = (T)(sign * h[i]);
   __syncthreads();
+  // eight independent partial sums: eight loads in flight per thread (the
+  // coarse levels' GMRES has up to 40 short vectors, where one dependent
+  // chain of loads and FMAs set the time)
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-    T s = w[j];
-    for (int i = 0; i < m; ++i) s = fma(c[i], V[(int64_t)i * ldv + j], s);
-    w[j] = s;
+    T s[8] = {w[j], T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    int i = 0;
+    for (; i + 8 <= m; i += 8) {
+      T a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = V[(int64_t)(i + u) * ldv + j];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s[u] = fma(c[i + u], a[u], s[u]);
+    }
+    for (; i < m; ++i) s[i & 7] = fma(c[i], V[(int64_t)i * ldv + j], s[i & 7]);
+    w[j] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
   }
 }
 // subtract the mean of the pressure component (stride d+1) given its sum
