@@ -399,6 +399,8 @@ typedef struct {
   int    status;              /* mf_status of the solve */
   int    fallback_newton_iters; /* mf_batch_solve_step: Newton iterations of the adaptive fallback
                                    (included in newton_iters; 0 when none ran) */
+  int    fallback_restarted;  /* mf_batch_solve_step: 1 when the fallback started over from the
+                                 initial guess (res_norm then continues from ||R_0|| again) */
 } mf_solve_report;
 
 void mf_solver_defaults(mf_solver_opts* o);
@@ -564,8 +566,10 @@ mf_status mf_batch_apply_jacobian(mf_batch* b, const void* const* xs, void* cons
  * With so->batch_fallback = 1 (default), an instance that has not converged
  * when the batched loop ends continues alone with mf_solve_step (adaptive
  * FGMRES(max(restart, 30)), the same preconditioner with twice the multigrid
- * smoothing steps, at least 8, up to max(max_newton, 40) iterations) from its
- * last iterate until ||R_i|| <= newton_rtol ||R_i,0||; its report then covers both parts
+ * smoothing steps, at least 8, up to max(max_newton, 40) iterations) until
+ * ||R_i|| <= newton_rtol ||R_i,0||: from its last iterate if the batched
+ * iterations reached sqrt(newton_rtol) ||R_i,0||, else from its initial guess
+ * (a device copy taken at entry); its report then covers both parts
  * (fallback_newton_iters says how many iterations the fallback took).
  * Returns MF_OK when every instance converged, otherwise the first failing
  * instance's status (MF_ERR_NOT_CONVERGED or MF_ERR_NAN; ups then hold the
@@ -633,7 +637,10 @@ mf_status mf_mg_interpolate(mf_handle fine, const double* u_fine, double* u_coar
  * Per-kernel CUDA-event timers.  When enabled, every kernel the operator calls
  * launch is bracketed by events on its launch stream; mf_profile_read
  * synchronises on those events and returns, per kernel kind, the number of
- * launches and the summed device milliseconds since the last reset.
+ * launches and the summed device milliseconds since the last reset.  While
+ * profiling is on, a Jacobian apply runs its mortar kernel after the cell
+ * kernel on the caller's stream (otherwise the two run side by side on two
+ * streams), so that each kernel's events bracket that kernel alone.
  * Kinds: 0 cell Jacobian FP64, 1 cell Jacobian FP32, 2 mortar FP64, 3 mortar
  * FP32, 4 cell residual, 5 cell linearisation, 6 Dirichlet rows, 7 diagonal. */
 #define MF_PROF_KINDS 8

@@ -57,7 +57,8 @@ class MfSolverOpts(C.Structure):
 class MfSolveReport(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("lin_iters_total", C.c_int), ("lin_iters", C.c_int * 64),
                 ("res_norm", C.c_double * 65), ("lambda_max", C.c_double), ("seconds", C.c_double),
-                ("status", C.c_int), ("fallback_newton_iters", C.c_int)]
+                ("status", C.c_int), ("fallback_newton_iters", C.c_int),
+                ("fallback_restarted", C.c_int)]
 
 
 STEP_RECORD_FIELDS = ("kinetic_energy", "dissipation", "dissipation_sym", "torque_still", "torque_moving", "power",

@@ -21,9 +21,6 @@
 #pragma once
 #include "mf_cell.cuh"
 
-#ifndef MF_LANE_STAGE
-#define MF_LANE_STAGE 1       // stage each point's coefficients in shared memory one point ahead
-#endif
 #ifndef MF_LANE_MINB_Q2
 #define MF_LANE_MINB_Q2 2     // Q2: two 288-thread blocks per SM (96 registers, no spills)
 #endif
@@ -36,12 +33,7 @@ template <int K> struct LaneCfg {
   static constexpr int THREADS = N2 * CB;       // one warp per cross-section position
   static constexpr int PLANES = 21;             // shared planes of NQ x CB floats
   static constexpr int MINB = THREADS <= 128 ? 4 : THREADS <= 288 ? MF_LANE_MINB_Q2 : 1;   // resident blocks asked of ptxas
-  // per-warp staging of the next point's coefficients (cp.async), where it
-  // fits beside the planes without costing a resident block (Q1, Q2)
-  static constexpr bool STAGE = MF_LANE_STAGE && K <= 2;
-  static constexpr int STAGE_FLOATS = STAGE ? N2 * 29 * CB : 0;
-  static constexpr int STAGE_OFF = (PLANES * NQ * CB + 3 * N * N + 3) / 4 * 4;   // floats; 16-byte aligned
-  static constexpr size_t SMEM = sizeof(float) * ((size_t)STAGE_OFF + STAGE_FLOATS);
+  static constexpr size_t SMEM = sizeof(float) * (size_t)PLANES * NQ * CB + sizeof(float) * 3 * N * N;
 };
 
 // Fields of the lane-layout FP32 cache (a subset of Cache<3>; G recomputed).
@@ -50,26 +42,6 @@ struct LaneCache {
   // field of Cache<3> that lane field f copies
   __host__ __device__ static constexpr int src(int f) { return f < 10 ? f : f + Sym<3>::n; }
 };
-
-// Copy the NF coefficient lines of point p (32 lanes each, one 128-byte line
-// per field) from the block's lane cache into this warp's staging buffer:
-// 16-byte cp.async chunks, 8 per line, spread over the warp's lanes.
-// Lane l copies part l % 8 of the lines of fields l / 8 + 4 j; everything is
-// recomputed from the block and thread index so that nothing stays live.
-template <int NQ>
-__device__ __forceinline__ void lane_stage_issue(const float* __restrict__ lc, uint32_t stage_base, int p) {
-  constexpr int NF = LaneCache::NF;
-  const int lane = threadIdx.x & 31, part = lane & 7, f0 = lane >> 3;
-  const float* src = lc + ((int64_t)blockIdx.x * NF * NQ + (int64_t)f0 * NQ + p) * 32 + part * 4;
-  const uint32_t dst = stage_base + (uint32_t)((f0 * 32 + part * 4) * 4);
-#pragma unroll
-  for (int j = 0; j < (NF + 3) / 4; ++j)
-    if (f0 + 4 * j < NF)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + (uint32_t)(j * 4 * 32 * 4)),
-                   "l"(src + (int64_t)j * 4 * NQ * 32)
-                   : "memory");
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
 
 // FP32 lane cache from the FP64 point-fastest cache: out index
 // ((blk * NF + f) * NQ + p) * 32 + lane for cell blk * 32 + lane (zero past nc).
@@ -132,9 +104,6 @@ k_cell_jac_lane(const int32_t* __restrict__ lcells, int64_t nc, const float* __r
   auto sp = [&](int pl, int p) -> float& { return S[(pl * NQ + p) * CB + lane]; };
   const float* lcb = lc + (int64_t)blockIdx.x * LC::NF * NQ * CB + lane;
   const int32_t* lcl = lcells + (int64_t)blockIdx.x * NQ * CB + lane;
-  float* stage = smem + L::STAGE_OFF + (L::STAGE ? t * LC::NF * CB : 0);
-  if constexpr (L::STAGE)   // first point of the pencil: in flight during the gather and the four sweeps
-    lane_stage_issue<NQ>(lc, (uint32_t)__cvta_generic_to_shared(stage), u0 + N * u1);
 
   // ---- gather the pencil's nodal values (wall velocities as zero)
   int node[N];
@@ -292,41 +261,25 @@ k_cell_jac_lane(const int32_t* __restrict__ lcells, int64_t nc, const float* __r
         H[c][4] = hxz;
         H[c][5] = hyz;
       }
-      // coefficients of this point: from the warp's staging buffer (copied
-      // one point ahead), else straight from the lane cache (one 128-byte
-      // line per field either way)
+      // coefficients of this point (coalesced: one 128-byte line per field)
       float Ji[3][3], a[3], gU[3][3], Rs[3], G[6], ct[3];
-      const float* cq;
-      int fs;                                             // stride between fields
-      if constexpr (L::STAGE) {
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
-        __syncwarp();
-        cq = stage + lane;
-        fs = CB;
-      } else {
-        cq = lcb + p * CB;
-        fs = NQ * CB;
-      }
+      const float* cq = lcb + p * CB;
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int m = 0; m < 3; ++m) Ji[r][m] = cq[(LC::JINV + r * 3 + m) * fs];
-      const float Wq = cq[LC::W * fs];
+        for (int m = 0; m < 3; ++m) Ji[r][m] = cq[(LC::JINV + r * 3 + m) * NQ * CB];
+      const float Wq = cq[LC::W * NQ * CB];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) ct[r] = cq[(LC::CT + r) * fs];
+      for (int r = 0; r < 3; ++r) ct[r] = cq[(LC::CT + r) * NQ * CB];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) a[m] = cq[(LC::A + m) * fs];
+      for (int m = 0; m < 3; ++m) a[m] = cq[(LC::A + m) * NQ * CB];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int m = 0; m < 3; ++m) gU[c][m] = cq[(LC::GU + c * 3 + m) * fs];
+        for (int m = 0; m < 3; ++m) gU[c][m] = cq[(LC::GU + c * 3 + m) * NQ * CB];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) Rs[c] = cq[(LC::RS + c) * fs];
-      const float tau = cq[LC::TAU * fs];
-      if constexpr (L::STAGE) {
-        __syncwarp();                                     // every lane has its values: refill the buffer
-        if (k + 1 < N) lane_stage_issue<NQ>(lc, (uint32_t)__cvta_generic_to_shared(stage), p + N2);
-      }
+      for (int c = 0; c < 3; ++c) Rs[c] = cq[(LC::RS + c) * NQ * CB];
+      const float tau = cq[LC::TAU * NQ * CB];
 #pragma unroll
       for (int e = 0; e < 6; ++e) {
         const int r = sym_r(3, e), s2 = sym_s(3, e);

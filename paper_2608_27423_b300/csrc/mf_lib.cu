@@ -689,9 +689,10 @@ static mf_status apply_t(mf_ctx* h, const typename IO<T>::type* x, typename IO<T
   const T* cache = std::is_same<T, double>::value ? (const T*)h->cache64
                  : std::is_same<T, float>::value ? (const T*)h->cache32 : (const T*)h->cachedf;
   CK(cudaMemsetAsync(y, 0, h->ndof * sizeof(TI), st));
-  if (MF_OVERLAP_MORTAR & (std::is_same<T, double>::value ? 1 : std::is_same<T, float>::value ? 2 : 4)) {
+  if (!h->prof && (MF_OVERLAP_MORTAR & (std::is_same<T, double>::value ? 1 : std::is_same<T, float>::value ? 2 : 4))) {
     // Both kernels scatter with atomics into the zeroed y: the mortar blocks
-    // run on the high-priority side stream, beside the cell kernel's waves.
+    // run on the high-priority side stream, beside the cell kernel's waves
+    // (serialised while profiling, so that each kernel's events time it alone).
     CK(cudaEventRecord(h->ev_fork, st));
     CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
     MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 0, x, y, 1, h->side)));
@@ -823,6 +824,8 @@ struct mf_batch {
   int sol_m = 0;
   double* norms2 = nullptr;                    // device [n] ||R_i||^2
   double* h_norms2 = nullptr;                  // pinned [n]
+  std::vector<double*> u_start;                // device copies of the initial guesses (fallback restarts)
+  std::vector<int64_t> u_start_n;
 };
 
 template <int D, int K>
@@ -884,6 +887,7 @@ extern "C" mf_status mf_batch_destroy(mf_batch* b) {
   if (b->sol_tab) cudaFree(b->sol_tab);
   if (b->sol_mtab) cudaFree(b->sol_mtab);
   if (b->norms2) cudaFree(b->norms2);
+  for (double* p : b->u_start) if (p) cudaFree(p);
   if (b->h_norms2) cudaFreeHost(b->h_norms2);
   delete b;
   return MF_OK;

@@ -235,6 +235,45 @@ __global__ void k_mdot_part(int64_t n, const T* __restrict__ V, int64_t ldv, con
     if (threadIdx.x == 0) part[(int64_t)i * gridDim.x + blockIdx.x] = s;
   }
 }
+// Short vectors: out[i] = V_i . w with one block per vector (no second pass);
+// four independent accumulators per thread keep four loads in flight.
+template <typename T>
+__global__ void k_mdot_block(int64_t n, const T* __restrict__ V, int64_t ldv, const T* __restrict__ w,
+                             double* __restrict__ out) {
+  const int i = blockIdx.x;
+  const T* v = V + (int64_t)i * ldv;
+  T a[4] = {T(0), T(0), T(0), T(0)};
+  const int64_t stride = blockDim.x;
+  int64_t j = threadIdx.x;
+  for (; j + 3 * stride < n; j += 4 * stride) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] = fma(v[j + u * stride], w[j + u * stride], a[u]);
+  }
+  for (; j < n; j += stride) a[0] = fma(v[j], w[j], a[0]);
+  double s = ((double)a[0] + (double)a[1]) + ((double)a[2] + (double)a[3]);
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) out[i] = s;
+  }
+}
+// y = x / sqrt(*nrm2) and z = d * y in one pass (the next Arnoldi column and
+// its inverse-diagonal preconditioning)
+template <typename T>
+__global__ void k_scale_by_mul(int64_t n, const T* __restrict__ x, T* __restrict__ y, const double* __restrict__ nrm2,
+                               const T* __restrict__ d, T* __restrict__ z) {
+  const double nn = *nrm2;
+  const T inv = nn > 1e-300 ? (T)(1.0 / sqrt(nn)) : T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = x[i] * inv;
+    y[i] = v;
+    z[i] = d[i] * v;
+  }
+}
 // out[i] (+)= sum_b part[i][b]  (one block per vector, fixed order: deterministic)
 __global__ void k_mdot_final(const double* __restrict__ part, int nb, double* __restrict__ out, int accumulate) {
   const int i = blockIdx.x;
