@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--max-newton", type=int, default=20)
     ap.add_argument("--mg-levels", type=int, default=4)
+    ap.add_argument("--mg-smooth", type=int, default=4, help="GMRES smoothing steps per level (solve leg)")
+    ap.add_argument("--mg-coarse-iters", type=int, default=40, help="coarsest-level GMRES dimension (solve leg)")
     ap.add_argument("--batched", action="store_true", help="also time 12 uneven instances, batched vs one by one")
     ap.add_argument("--transient", type=int, default=0, help="also run this many graph-captured BDF2 time steps")
     ap.add_argument("--transient-newton", type=int, default=3, help="Newton iterations per transient step")
@@ -69,6 +71,9 @@ def parse():
     ap.add_argument("--q3-workload", default="3d_q3", help="the Q3 workload of the q3 leg")
     ap.add_argument("--no-q3", action="store_true", help="skip the Q3 leg")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core interpolation probe")
+    ap.add_argument("--tc-only", action="store_true",
+                    help="run only the tensor-core interpolation probe and print its JSON (launch order: 3 checks, "
+                         "6 warm-ups, then the timed FMA, TF32 and 3xTF32 launches)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default cells per block (profiling runs: timings under ncu are not representative)")
     return ap.parse_args()
@@ -219,7 +224,8 @@ def solve_leg(args, op, mesh, prm, f, T, workload=None):
             continue
         o = solver_defaults(theta=prm["theta"], pc=MF_PC_MG, pc_precision=pcp, newton_rtol=1e-8,
                             max_newton=args.max_newton, lin_rtol=1e-2, restart=30, max_lin_iters=150,
-                            mg_smooth=4, mg_coarse_iters=40, outer_precision=outer, mg_smoother=smoother)
+                            mg_smooth=args.mg_smooth, mg_coarse_iters=args.mg_coarse_iters, outer_precision=outer,
+                            mg_smoother=smoother)
         # the first solve of a variant also allocates its workspaces and
         # captures its V-cycle graph; the timed one is the next, from the
         # same initial guess (as every later time step would run)
@@ -568,11 +574,13 @@ def tc_leg(args):
     names = {0: "fp32_fma_sum_factorised", 1: "tcgen05_tf32", 2: "tcgen05_3xtf32"}
     for v in (0, 1, 2):
         contract_probe(v, u[:148], outs[v], reps=1, err=err)
-    for v in (0, 1, 2):
+    for v in (0, 1, 2):                     # warm-up: every variant twice, then one timed launch of each
         blocks, reps = launch[v]
         for _ in range(2):
             contract_probe(v, u[:blocks], sums[:blocks], reps=reps, err=err)
-        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    for v in (0, 1, 2):
+        blocks, reps = launch[v]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         contract_probe(v, u[:blocks], sums[:blocks], reps=reps, err=err)
@@ -806,6 +814,9 @@ def main():
     from paper_2608_27423_b300 import RotorStatorOperator, MF_FP32, MF_FP64, solver_defaults, MF_PC_JACOBI, \
         MF_PC_CHEBYSHEV
     from paper_2608_27423_b300 import build as _b
+    if args.tc_only:
+        print(json.dumps({"interpolation_tensor_cores": tc_leg(args)}), flush=True)
+        return
     mesh, prm, f = build_inputs(args.workload)
     dev = torch.device("cuda", local)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)

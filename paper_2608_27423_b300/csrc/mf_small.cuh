@@ -236,7 +236,8 @@ __global__ void k_mdot_part(int64_t n, const T* __restrict__ V, int64_t ldv, con
   }
 }
 // Short vectors: out[i] = V_i . w with one block per vector (no second pass);
-// four independent accumulators per thread keep four loads in flight.
+// four independent accumulators per thread keep four loads in flight.  Any
+// block size that is a multiple of 32, up to 1024.
 template <typename T>
 __global__ void k_mdot_block(int64_t n, const T* __restrict__ V, int64_t ldv, const T* __restrict__ w,
                              double* __restrict__ out) {
