@@ -312,7 +312,13 @@ __global__ void k_maxpy(int64_t n, int m, const T* __restrict__ V, int64_t ldv, 
 #pragma unroll
       for (int u = 0; u < 8; ++u) s[u] = fma(c[i + u], a[u], s[u]);
     }
-    for (; i < m; ++i) s[i & 7] = fma(c[i], V[(int64_t)i * ldv + j], s[i & 7]);
+    // the remainder on two fixed accumulators (a dynamic index would put s in local memory)
+    for (; i + 2 <= m; i += 2) {
+      const T a0 = V[(int64_t)i * ldv + j], a1 = V[(int64_t)(i + 1) * ldv + j];
+      s[0] = fma(c[i], a0, s[0]);
+      s[1] = fma(c[i + 1], a1, s[1]);
+    }
+    if (i < m) s[2] = fma(c[i], V[(int64_t)i * ldv + j], s[2]);
     w[j] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
   }
 }
