@@ -148,3 +148,7 @@ def test_batched_solve_fallback_finishes_instances(cases):
         k = r.newton_iters
         assert r.status == 0 and r.fallback_newton_iters >= 1 and k == 2 + r.fallback_newton_iters
         assert r.res_norm[k] <= tol * r.res_norm[0] * (1 + 1e-12)
+        # the fallback starts over from the initial guess unless the batched
+        # iterations got within sqrt(newton_rtol) of the target
+        best = min(r.res_norm[1], r.res_norm[2], r.res_norm[0])
+        assert r.fallback_restarted == (0 if best <= np.sqrt(tol) * r.res_norm[0] else 1)
