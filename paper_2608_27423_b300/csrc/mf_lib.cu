@@ -21,6 +21,16 @@
 
 using namespace mf;
 
+#ifndef MF_OVERLAP_MORTAR
+#define MF_OVERLAP_MORTAR 7   // precisions whose apply runs the mortar beside the cell kernel: 1 FP64, 2 FP32, 4 DF64
+#endif
+#ifndef MF_OVERLAP_ORDER
+// 1: the cell kernel is launched first and the mortar on a low-priority side
+//    stream fills the room its blocks leave on each SM; 0: the mortar first, on
+//    a high-priority side stream
+#define MF_OVERLAP_ORDER 1
+#endif
+
 #include "mf_log.inc"
 
 struct mf_mesh {
@@ -525,7 +535,7 @@ extern "C" mf_status mf_create(const mf_mesh* m, int k, double nu, double omega,
     }
     int prio_lo = 0, prio_hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, MF_OVERLAP_ORDER == 1 ? prio_lo : prio_hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
       return fail(MF_ERR_CUDA);
@@ -680,9 +690,6 @@ extern "C" mf_status mf_wall_loads(mf_handle h, const double* up, const uint8_t*
   return wall_loads_from_rows(h, up, h->react, group, n_groups, out, st);
 }
 
-#ifndef MF_OVERLAP_MORTAR
-#define MF_OVERLAP_MORTAR 7   // precisions whose apply runs the mortar beside the cell kernel: 1 FP64, 2 FP32, 4 DF64
-#endif
 template <typename T>
 static mf_status apply_t(mf_ctx* h, const typename IO<T>::type* x, typename IO<T>::type* y, cudaStream_t st) {
   using TI = typename IO<T>::type;
@@ -691,12 +698,17 @@ static mf_status apply_t(mf_ctx* h, const typename IO<T>::type* x, typename IO<T
   CK(cudaMemsetAsync(y, 0, h->ndof * sizeof(TI), st));
   if (!h->prof && (MF_OVERLAP_MORTAR & (std::is_same<T, double>::value ? 1 : std::is_same<T, float>::value ? 2 : 4))) {
     // Both kernels scatter with atomics into the zeroed y: the mortar blocks
-    // run on the high-priority side stream, beside the cell kernel's waves
-    // (serialised while profiling, so that each kernel's events time it alone).
+    // run on the side stream, beside the cell kernel's waves (serialised
+    // while profiling, so that each kernel's events time it alone).
     CK(cudaEventRecord(h->ev_fork, st));
     CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-    MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 0, x, y, 1, h->side)));
-    MF_DISPATCH(h->d, h->k, (launch_jac<D, K, T>(h, cache, x, y, st)));
+    if (MF_OVERLAP_ORDER == 1) {
+      MF_DISPATCH(h->d, h->k, (launch_jac<D, K, T>(h, cache, x, y, st)));
+      MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 0, x, y, 1, h->side)));
+    } else {
+      MF_DISPATCH(h->d, h->k, (launch_mortar<D, K, T>(h, 0, x, y, 1, h->side)));
+      MF_DISPATCH(h->d, h->k, (launch_jac<D, K, T>(h, cache, x, y, st)));
+    }
     CK(cudaEventRecord(h->ev_join, h->side));
     CK(cudaStreamWaitEvent(st, h->ev_join, 0));
   } else {
