@@ -763,6 +763,20 @@ def cpu_oracle_rate_all_cores(name, seconds, pool=None):
     return n_dofs / t_full, sample, procs
 
 
+def cpu_model():
+    """The host CPU's model string (/proc/cpuinfo) and logical core count."""
+    name = "unknown"
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.startswith("model name"):
+                    name = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": name, "logical_cores": os.cpu_count()}
+
+
 def cpu_oracle_2d():
     """The oracle's two evaluation paths on the whole 2D workload (576 + 768 Q2
     quads): (A) element matrices assembled to CSR, then SpMV; (B) the
@@ -1000,7 +1014,15 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": "DoFs/s", "cores": procs, "kind": "oracle",
                                 "sample": sample,
                                 "single_process": {"value": rate1, "threads": cpu_cores_used(), "sample": sample1},
-                                "oracle_2d": cpu_oracle_2d()}
+                                "oracle_2d": cpu_oracle_2d(), "cpu_model": cpu_model()}
+        if not args.no_q3:
+            try:       # config 3: the Q3 cylinder, one process on a bounded sample
+                mq, pq, fq = build_inputs(args.q3_workload)
+                rq, sq, _ = cpu_oracle_rate(mq, pq, fq, max(4.0, args.cpu_seconds / 2))
+                line["cpu_baseline"]["single_process_q3"] = {"workload": args.q3_workload, "value": rq,
+                                                             "threads": cpu_cores_used(), "sample": sq}
+            except Exception as exc:
+                line["cpu_baseline"]["single_process_q3"] = {"error": repr(exc)}
     if rank == 0:
         print(json.dumps(line, default=float), flush=True)
     if dist:
