@@ -309,7 +309,12 @@ mf_status mf_residual(mf_handle h, const double* up, double* r, void* stream);
  * terms of Eqs. EqMortarPre, EqMortarDiff, EqMortarMass.  prec MF_FP64: x, y double; MF_FP32:
  * x, y float (FP32 cache); MF_DF64: x, y double, double-float arithmetic (its
  * cache copy is built on the first such call after each linearisation).  x entries on wall velocity DoFs are ignored as
- * inputs and copied to y (identity rows/columns).  x and y must not alias. */
+ * inputs and copied to y (identity rows/columns).  x and y must not alias.
+ * Asynchronous on `stream`: the mortar kernel runs on a side stream the
+ * handle owns, forked from `stream` and joined back to it with events, so
+ * the call is ordered on `stream` like a single launch and can be captured
+ * into a CUDA graph from `stream`; one handle must not run two applies on
+ * different streams at the same time. */
 mf_status mf_apply_jacobian(mf_handle h, const void* x, void* y, mf_precision prec, void* stream);
 
 /* diag(J) at the current linearisation (volume and mortar parts, Algorithm 1;
