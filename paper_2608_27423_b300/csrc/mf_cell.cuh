@@ -482,13 +482,18 @@ struct StateArgs {
 #ifndef MF_STATE_MINB
 #define MF_STATE_MINB 2      // resident blocks of the FP64 state kernel requested from the register allocator (2: 7-9 % faster than 1 at Q2/Q3)
 #endif
-template <int D, int K, int MODE>
+// GEO: the geometry fields of the cache (J^-1, det J w, G, ctil) are valid
+// for the current coordinates (an earlier pass at the same rotor angle wrote
+// them): read them instead of differentiating x twice and inverting J, and
+// leave them unwritten.  Bit-for-bit the values a recomputation would give.
+template <int D, int K, int MODE, bool GEO>
 __global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MF_STATE_MINB) k_cell_state(StateArgs A) {
   using C = CellCfg<D, K>;
   using T = double;
   constexpr int N = C::N, NQ = C::NQ, NF = D + 1;
   constexpr int NV = 3 * D + 1;          // x (D), u (D), p, h_t (D)
   constexpr int NS = 2 * D * D + D;      // largest plane count: gradients of x, u and p
+  constexpr int F0 = GEO ? D : 0;        // first differentiated field: x only without the geometry
   using CF = Cache<D>;
   __shared__ SmTab<N, T> st;
   __shared__ T smem[C::CPB][NS * NQ];
@@ -532,47 +537,65 @@ __global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MF_STATE_MINB) k_cell_
     line<D, N, NV, false>(tile, NQ, t, ii[r], strd[r], st.B, v);
     __syncthreads();
   }
-  // reference gradients of x, u, p (fields 0 .. 2D)
-  constexpr int NG = 2 * D + 1;
+  // reference gradients of x (unless GEO), u, p (fields F0 .. 2D)
+  constexpr int NG = 2 * D + 1, NGD = NG - F0;
   T dv[NG][D];
 #pragma unroll
-  for (int f = 0; f < NG; ++f) tile[f * NQ + t] = v[f];
+  for (int f = F0; f < NG; ++f) tile[(f - F0) * NQ + t] = v[f];
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < D; ++r) {
-    T o[NG];
-    line<D, N, NG, false>(tile, NQ, t, ii[r], strd[r], st.Dg, o);
+    T o[NGD];
+    line<D, N, NGD, false>(tile, NQ, t, ii[r], strd[r], st.Dg, o);
 #pragma unroll
-    for (int f = 0; f < NG; ++f) dv[f][r] = o[f];
+    for (int f = 0; f < NGD; ++f) dv[F0 + f][r] = o[f];
   }
   __syncthreads();
-  // reference Hessians of x and u (fields 0 .. 2D-1) from their gradients
+  // reference Hessians of x (unless GEO) and u (fields F0 .. 2D-1) from their gradients
+  constexpr int NH = 2 * D - F0;
   T H[2 * D][Sym<D>::n];
 #pragma unroll
-  for (int f = 0; f < 2 * D; ++f)
+  for (int f = 0; f < NH; ++f)
 #pragma unroll
-    for (int r = 0; r < D; ++r) tile[(f * D + r) * NQ + t] = dv[f][r];
+    for (int r = 0; r < D; ++r) tile[(f * D + r) * NQ + t] = dv[F0 + f][r];
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < Sym<D>::n; ++e) {
     const int r = sym_r(D, e), s = sym_s(D, e);
     const int base = t - ii[s] * strd[s];
-    T o[2 * D];
+    T o[NH];
 #pragma unroll
-    for (int f = 0; f < 2 * D; ++f) o[f] = T(0);
+    for (int f = 0; f < NH; ++f) o[f] = T(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
       const T m = st.Dg[ii[s]][j];
 #pragma unroll
-      for (int f = 0; f < 2 * D; ++f) o[f] = fma(m, tile[(f * D + r) * NQ + base + j * strd[s]], o[f]);
+      for (int f = 0; f < NH; ++f) o[f] = fma(m, tile[(f * D + r) * NQ + base + j * strd[s]], o[f]);
     }
 #pragma unroll
-    for (int f = 0; f < 2 * D; ++f) H[f][e] = o[f];
+    for (int f = 0; f < NH; ++f) H[F0 + f][e] = o[f];
   }
   __syncthreads();
 
-  // ---- geometry: J[m][r] = dv[m][r]
-  T Ji[D][D], detJ;
+  // ---- geometry: J[m][r] = dv[m][r], or the cached fields (GEO)
+  T Ji[D][D], Wq;
+  T G[Sym<D>::n];
+  T ct[D];
+  if constexpr (GEO) {
+    const int64_t Pn = A.nc * NQ;
+    const double* cq = A.cache + (active ? cell : 0) * NQ + t;
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int m = 0; m < D; ++m) Ji[r][m] = cq[(CF::JINV + r * D + m) * Pn];
+    Wq = cq[CF::W * Pn];
+#pragma unroll
+    for (int e = 0; e < Sym<D>::n; ++e) G[e] = cq[(CF::G + e) * Pn];
+#pragma unroll
+    for (int r = 0; r < D; ++r) ct[r] = cq[(CF::CT + r) * Pn];
+    if (active) atomicAdd(&vol[cl], Wq);
+  } else {
+  T detJ;
   if (D == 2) {
     const T j00 = dv[0][0], j01 = dv[0][1], j10 = dv[1][0], j11 = dv[1][1];
     detJ = j00 * j11 - j01 * j10;
@@ -606,10 +629,9 @@ __global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MF_STATE_MINB) k_cell_
       for (int m = 0; m < 3; ++m) Ji[r][m] = I[r][m];
   }
   const T wq = st.w[ii[0]] * st.w[ii[1]] * (D == 3 ? st.w[ii[2]] : T(1));
-  const T Wq = detJ * wq;
+  Wq = detJ * wq;
   if (active) atomicAdd(&vol[cl], Wq);
   // G = Jinv Jinv^T (symmetric, off-diagonals doubled for the contraction with H)
-  T G[Sym<D>::n];
 #pragma unroll
   for (int e = 0; e < Sym<D>::n; ++e) {
     const int r = sym_r(D, e), s = sym_s(D, e);
@@ -619,7 +641,6 @@ __global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MF_STATE_MINB) k_cell_
     G[e] = (r == s) ? g : T(2) * g;
   }
   // ctil_r = sum_m Jinv[r][m] (G : H_xi x_m)
-  T ct[D];
   {
     T cv[D];
 #pragma unroll
@@ -637,6 +658,7 @@ __global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MF_STATE_MINB) k_cell_
       ct[r] = s;
     }
   }
+  }   // geometry computed
   __syncthreads();
   const T V = vol[cl];
   const T h = (D == 2) ? sqrt(T(4) * V / T(M_PI)) : cbrt(T(6) * V / T(M_PI));
@@ -687,15 +709,17 @@ __global__ void __launch_bounds__(CellCfg<D, K>::THREADS, MF_STATE_MINB) k_cell_
     if (active) {
       const int64_t Pn = A.nc * NQ;
       double* cp = A.cache + cell * NQ + t;
+      if constexpr (!GEO) {
 #pragma unroll
-      for (int r = 0; r < D; ++r)
+        for (int r = 0; r < D; ++r)
 #pragma unroll
-        for (int m = 0; m < D; ++m) cp[(CF::JINV + r * D + m) * Pn] = Ji[r][m];
-      cp[CF::W * Pn] = Wq;
+          for (int m = 0; m < D; ++m) cp[(CF::JINV + r * D + m) * Pn] = Ji[r][m];
+        cp[CF::W * Pn] = Wq;
 #pragma unroll
-      for (int e = 0; e < Sym<D>::n; ++e) cp[(CF::G + e) * Pn] = G[e];
+        for (int e = 0; e < Sym<D>::n; ++e) cp[(CF::G + e) * Pn] = G[e];
 #pragma unroll
-      for (int r = 0; r < D; ++r) cp[(CF::CT + r) * Pn] = ct[r];
+        for (int r = 0; r < D; ++r) cp[(CF::CT + r) * Pn] = ct[r];
+      }
 #pragma unroll
       for (int m = 0; m < D; ++m) cp[(CF::A + m) * Pn] = a[m];
 #pragma unroll

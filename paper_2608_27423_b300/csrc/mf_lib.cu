@@ -118,6 +118,7 @@ struct mf_ctx {
   SegTable seg{nullptr, nullptr, nullptr, nullptr, nullptr};   // unequal partitions: segments of one layer
   int64_t nmwall = 0;  // the last nmwall entries of `wall` move with the rotor (blade walls)
   bool have_lin = false;
+  bool geo_valid = false;              // the cache's geometry fields match the current coordinates
   int ncache = 0;
   int nb = 0;  // blocks for reductions
   // device
@@ -233,9 +234,18 @@ static void launch_state(mf_ctx* h, int mode, const double* up, double* dst, cud
   using C = CellCfg<D, K>;
   const unsigned g = nblk(h->nc, C::CPB);
   ProfScope ps(h, mode == 0 ? 5 : 4, st);
-  if (mode == 0) k_cell_state<D, K, 0><<<g, C::THREADS, 0, st>>>(A);
-  else if (mode == 1) k_cell_state<D, K, 1><<<g, C::THREADS, 0, st>>>(A);
-  else k_cell_state<D, K, 2><<<g, C::THREADS, 0, st>>>(A);
+  // the cached geometry is reused while the coordinates have not moved since
+  // a cache-writing pass (apply_angle clears geo_valid)
+  if (h->geo_valid) {
+    if (mode == 0) k_cell_state<D, K, 0, true><<<g, C::THREADS, 0, st>>>(A);
+    else if (mode == 1) k_cell_state<D, K, 1, true><<<g, C::THREADS, 0, st>>>(A);
+    else k_cell_state<D, K, 2, true><<<g, C::THREADS, 0, st>>>(A);
+  } else {
+    if (mode == 0) k_cell_state<D, K, 0, false><<<g, C::THREADS, 0, st>>>(A);
+    else if (mode == 1) k_cell_state<D, K, 1, false><<<g, C::THREADS, 0, st>>>(A);
+    else k_cell_state<D, K, 2, false><<<g, C::THREADS, 0, st>>>(A);
+    if (mode != 1) h->geo_valid = true;
+  }
 }
 
 // The one-cell-per-lane FP32 kernel (mf_lane.cuh) exists for 3D, k = 1..3;
@@ -461,6 +471,7 @@ extern "C" const char* mf_last_error(mf_handle h) { return h ? h->err.c_str() : 
 static mf_status apply_angle(mf_ctx* h, double theta, cudaStream_t st) {
   h->theta = theta;
   h->df_valid = false;
+  h->geo_valid = false;
   const double ct = cos(theta), sn = sin(theta);
   const double* td = h->theta_on_dev ? h->d_theta : nullptr;
   if (h->d == 2) k_rotate<2><<<nblk(h->nn, 256), 256, 0, st>>>(h->x0, h->node_side, h->x, h->nn, ct, sn, td);
