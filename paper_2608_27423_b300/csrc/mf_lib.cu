@@ -119,6 +119,7 @@ struct mf_ctx {
   int64_t nmwall = 0;  // the last nmwall entries of `wall` move with the rotor (blade walls)
   bool have_lin = false;
   bool geo_valid = false;              // the cache's geometry fields match the current coordinates
+  bool angle_set = false;              // coordinates, mortar map and face geometry are at the host angle `theta`
   int ncache = 0;
   int nb = 0;  // blocks for reductions
   // device
@@ -470,6 +471,7 @@ extern "C" const char* mf_last_error(mf_handle h) { return h ? h->err.c_str() : 
 
 static mf_status apply_angle(mf_ctx* h, double theta, cudaStream_t st) {
   h->theta = theta;
+  h->angle_set = !h->theta_on_dev;
   h->df_valid = false;
   h->geo_valid = false;
   const double ct = cos(theta), sn = sin(theta);
@@ -617,8 +619,13 @@ extern "C" mf_status mf_set_linearization(mf_handle h, const double* up_star, do
   if (!h || !up_star) return MF_ERR_ARG;
   if (!std::isfinite(theta)) { h->err = "theta must be finite"; return MF_ERR_ARG; }
   cudaStream_t st = S(stream);
-  mf_status s = apply_angle(h, theta, st);
-  if (s != MF_OK) return s;
+  // the rotation, mortar map and face geometry depend on the angle only: a
+  // relinearisation at the angle already applied (the Newton loop's levels)
+  // keeps them, and the state pass keeps the cached cell geometry too
+  if (!(h->angle_set && !h->theta_on_dev && theta == h->theta)) {
+    mf_status s = apply_angle(h, theta, st);
+    if (s != MF_OK) return s;
+  }
   MF_DISPATCH(h->d, h->k, (launch_state<D, K>(h, 0, up_star, nullptr, st)));
   const int64_t ncv = (int64_t)h->ncache * h->nc * ipow(h->k + 1, h->d);
   k_cast<double, float><<<nblk(ncv, 256), 256, 0, st>>>(h->cache64, h->cache32, ncv);
