@@ -10,9 +10,9 @@
 //   x-line   (j, k) = (t % N, t / N): the points (0..N-1, j, k),
 //   y-line   (i, k) = (t % N, t / N): the points (i, 0..N-1, k).
 // Contractions along a thread's own line run in registers (N loads give N
-// outputs, not one), the z-direction never leaves the registers, and shared
-// memory is laid out [plane][point][lane] so every access of a warp touches 32
-// consecutive words (no bank conflicts whatever the point pattern).  The
+// outputs, not one), and shared memory is laid out [plane][point][lane] so
+// every access of a warp touches 32 consecutive words (no bank conflicts
+// whatever the point pattern).  The
 // per-point coefficients come from an FP32 copy of the linearisation cache in
 // the same lane-interleaved layout, [block][field][point][lane], so each warp
 // load is one 128-byte line; G = J^-1 J^-T is recomputed instead of read
@@ -222,27 +222,31 @@ k_cell_jac_lane(const int32_t* __restrict__ lcells, int64_t nc, const float* __r
     }
   }
   __syncthreads();
-  // ---- pencil (i, j): z-derivatives in registers, point physics, z-transpose
+  // ---- pencil (i, j): point physics, z-transpose.  The pencil's values and
+  // x/y-derivatives stay in shared memory and are read per point (the thread
+  // owns every entry of its pencil, so nothing else touches them in this
+  // phase); the outputs of point k go to its own Hessian slots, which no
+  // later point reads: Fx[.][0] -> planes 15..18, Fx[.][1] -> planes 19, 20,
+  // 8, 9; the z-transposed sums g -> planes 0..3 after the last point.
   {
-    float V[N][4], Vy[N][4], Vx[N][4], gz[N][4];
+    float gz[N][4];
+#pragma unroll
+    for (int c = 0; c < N; ++c)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) gz[c][f] = 0.f;
+    const int p0 = u0 + N * u1;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      const int p = u0 + N * u1 + N2 * k;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) { V[k][f] = sp(f, p); Vy[k][f] = sp(4 + f, p); Vx[k][f] = sp(11 + f, p); gz[k][f] = 0.f; }
-    }
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int p = u0 + N * u1 + N2 * k;
+      const int p = p0 + N2 * k;
       float v[4], dv[4][3], H[3][6];
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         float gzf = 0.f;
 #pragma unroll
-        for (int c = 0; c < N; ++c) gzf = fmaf(sDg[k][c], V[c][f], gzf);
-        v[f] = V[k][f];
-        dv[f][0] = Vx[k][f];
-        dv[f][1] = Vy[k][f];
+        for (int c = 0; c < N; ++c) gzf = fmaf(sDg[k][c], sp(f, p0 + N2 * c), gzf);
+        v[f] = sp(f, p);
+        dv[f][0] = sp(11 + f, p);
+        dv[f][1] = sp(4 + f, p);
         dv[f][2] = gzf;
       }
 #pragma unroll
@@ -250,9 +254,10 @@ k_cell_jac_lane(const int32_t* __restrict__ lcells, int64_t nc, const float* __r
         float hzz = 0.f, hxz = 0.f, hyz = 0.f;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          hzz = fmaf(sD2[k][j], V[j][c], hzz);
-          hxz = fmaf(sDg[k][j], Vx[j][c], hxz);
-          hyz = fmaf(sDg[k][j], Vy[j][c], hyz);
+          const int pj = p0 + N2 * j;
+          hzz = fmaf(sD2[k][j], sp(c, pj), hzz);
+          hxz = fmaf(sDg[k][j], sp(11 + c, pj), hxz);
+          hyz = fmaf(sDg[k][j], sp(4 + c, pj), hyz);
         }
         H[c][0] = sp(15 + c, p);
         H[c][1] = sp(8 + c, p);
@@ -295,23 +300,26 @@ k_cell_jac_lane(const int32_t* __restrict__ lcells, int64_t nc, const float* __r
         gz[k][f] += fv[f];
 #pragma unroll
         for (int c = 0; c < N; ++c) gz[c][f] = fmaf(sDg[k][c], Fx[f][2], gz[c][f]);
-        sp(f, p) = Fx[f][0];                                // own pencil point: V already in registers
-        sp(4 + f, p) = Fx[f][1];                            // Vy likewise
+        sp(15 + f, p) = Fx[f][0];
       }
+      sp(19, p) = Fx[0][1];
+      sp(20, p) = Fx[1][1];
+      sp(8, p) = Fx[2][1];
+      sp(9, p) = Fx[3][1];
     }
 #pragma unroll
     for (int c = 0; c < N; ++c)
 #pragma unroll
-      for (int f = 0; f < 4; ++f) sp(8 + f, u0 + N * u1 + N2 * c) = gz[c][f];
+      for (int f = 0; f < 4; ++f) sp(f, p0 + N2 * c) = gz[c][f];
   }
   __syncthreads();
-  {  // x-line: g += Dg_x^T Fx[.][0]
+  {  // x-line: g += Dg_x^T Fx[.][0]   (Fx0 in planes 15..18, g in planes 0..3)
     float fx[N][4], g[N][4];
 #pragma unroll
     for (int a = 0; a < N; ++a) {
       const int p = a + N * u0 + N2 * u1;
 #pragma unroll
-      for (int f = 0; f < 4; ++f) { fx[a][f] = sp(f, p); g[a][f] = sp(8 + f, p); }
+      for (int f = 0; f < 4; ++f) { fx[a][f] = sp(15 + f, p); g[a][f] = sp(f, p); }
     }
 #pragma unroll
     for (int a = 0; a < N; ++a) {
@@ -321,18 +329,19 @@ k_cell_jac_lane(const int32_t* __restrict__ lcells, int64_t nc, const float* __r
         float s = g[a][f];
 #pragma unroll
         for (int q = 0; q < N; ++q) s = fmaf(sDg[q][a], fx[q][f], s);
-        sp(8 + f, p) = s;
+        sp(f, p) = s;
       }
     }
   }
   __syncthreads();
-  {  // y-line: g += Dg_y^T Fx[.][1], then B^T along y
+  {  // y-line: g += Dg_y^T Fx[.][1] (planes 19, 20, 8, 9), then B^T along y -> planes 0..3
+    constexpr int FY[4] = {19, 20, 8, 9};
     float fy[N][4], g[N][4];
 #pragma unroll
     for (int b = 0; b < N; ++b) {
       const int p = u0 + N * b + N2 * u1;
 #pragma unroll
-      for (int f = 0; f < 4; ++f) { fy[b][f] = sp(4 + f, p); g[b][f] = sp(8 + f, p); }
+      for (int f = 0; f < 4; ++f) { fy[b][f] = sp(FY[f], p); g[b][f] = sp(f, p); }
     }
 #pragma unroll
     for (int b = 0; b < N; ++b)
@@ -353,16 +362,16 @@ k_cell_jac_lane(const int32_t* __restrict__ lcells, int64_t nc, const float* __r
         for (int f = 0; f < 4; ++f) o[f] = fmaf(m, g[b][f], o[f]);
       }
 #pragma unroll
-      for (int f = 0; f < 4; ++f) sp(8 + f, u0 + N * c + N2 * u1) = o[f];
+      for (int f = 0; f < 4; ++f) sp(f, u0 + N * c + N2 * u1) = o[f];
     }
   }
   __syncthreads();
-  {  // x-line: B^T along x
+  {  // x-line: B^T along x (planes 0..3)
     float h[N][4];
 #pragma unroll
     for (int a = 0; a < N; ++a)
 #pragma unroll
-      for (int f = 0; f < 4; ++f) h[a][f] = sp(8 + f, a + N * u0 + N2 * u1);
+      for (int f = 0; f < 4; ++f) h[a][f] = sp(f, a + N * u0 + N2 * u1);
 #pragma unroll
     for (int c = 0; c < N; ++c) {
       float o[4] = {0.f, 0.f, 0.f, 0.f};
@@ -373,7 +382,7 @@ k_cell_jac_lane(const int32_t* __restrict__ lcells, int64_t nc, const float* __r
         for (int f = 0; f < 4; ++f) o[f] = fmaf(m, h[a][f], o[f]);
       }
 #pragma unroll
-      for (int f = 0; f < 4; ++f) sp(8 + f, c + N * u0 + N2 * u1) = o[f];
+      for (int f = 0; f < 4; ++f) sp(f, c + N * u0 + N2 * u1) = o[f];
     }
   }
   __syncthreads();
@@ -383,7 +392,7 @@ k_cell_jac_lane(const int32_t* __restrict__ lcells, int64_t nc, const float* __r
 #pragma unroll
     for (int k = 0; k < N; ++k)
 #pragma unroll
-      for (int f = 0; f < 4; ++f) h[k][f] = sp(8 + f, u0 + N * u1 + N2 * k);
+      for (int f = 0; f < 4; ++f) h[k][f] = sp(f, u0 + N * u1 + N2 * k);
     if (active) {
 #pragma unroll
       for (int c = 0; c < N; ++c) {
