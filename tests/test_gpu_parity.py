@@ -186,3 +186,23 @@ def test_apply_before_linearization_is_an_error():
     x = torch.zeros(mesh.n_dofs, dtype=torch.float64, device="cuda")
     with pytest.raises(MfError):
         g.apply_jacobian(x, torch.empty_like(x))
+
+
+@pytest.mark.parametrize("c", CASES, ids=cid)
+def test_residual_with_cached_geometry_equals_recomputed(c):
+    """After a cache-writing pass at the current angle the state kernel reads
+    J^-1, det J w, G and c-tilde from the cache instead of recomputing them;
+    the residual must not change (up to the atomic scatter's summation order)
+    and must still match the oracle.  set_angle clears the cached geometry,
+    so the first residual recomputes it."""
+    mesh, prm, f, op, g, T = setup(**c)
+    up = T(f["up_star"] * 0.7 + 0.1)
+    g.set_angle(prm["theta"])
+    r_fresh = torch.empty_like(up)
+    g.residual(up, r_fresh)                      # geometry recomputed
+    g.set_linearization(T(f["up_star"]), prm["theta"])   # same angle: writes the geometry cache
+    r_cached = torch.empty_like(up)
+    g.residual(up, r_cached)                     # geometry read from the cache
+    a, b = r_cached.cpu().numpy(), r_fresh.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+    assert rel(a, op.residual(f["up_star"] * 0.7 + 0.1)) <= TOL64
