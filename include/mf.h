@@ -209,6 +209,23 @@ mf_status mf_mesh_slab(const mf_mesh* m, int n_parts, int part, mf_mesh** out, m
 mf_status mf_halo_pack(const double* y, const int32_t* idx, int64_t n, int nf, double* buf, void* stream);
 mf_status mf_halo_add(double* y, const int32_t* idx, const uint8_t* wall, int64_t n, int nf, const double* buf,
                       void* stream);
+/* Krylov vector kernels for a solver that spans the parts (the z-slab
+ * FGMRES of the Python package: these kernels do its vector arithmetic, the
+ * caller all-reduces the dot products).  FP64 device vectors of length n;
+ * V holds m vectors, vector i at V + i ldv.  Asynchronous on `stream`.
+ *   mf_vec_dots:  out[i] = sum_j w[j] V_i[j] x[j], i < m (w NULL: weights
+ *                 1; the weights count each shared row once over the parts);
+ *                 out: device, m doubles; fixed summation order.
+ *   mf_vec_maxpy: y += sign sum_{i<m} c[i] V_i (c: device, m doubles).
+ *   mf_vec_axpby: y = a x + b y (host scalars).
+ *   mf_vec_mul:   z = d * v entrywise (an inverse-diagonal preconditioner).
+ * MF_ERR_ARG for n < 0, m < 1 or m > 256, ldv < n, or a null pointer. */
+mf_status mf_vec_dots(int64_t n, const double* V, int64_t ldv, int m, const double* x, const double* w, double* out,
+                      void* stream);
+mf_status mf_vec_maxpy(int64_t n, const double* V, int64_t ldv, int m, const double* c, double sign, double* y,
+                       void* stream);
+mf_status mf_vec_axpby(int64_t n, double a, const double* x, double b, double* y, void* stream);
+mf_status mf_vec_mul(int64_t n, const double* d, const double* v, double* z, void* stream);
 
 /* ---------------------------------------------------------------- per-call metrics log
  * mf_log_open(path): from now on the mesh generator, mf_solve_step,

@@ -236,6 +236,32 @@ def contract_probe(variant, u, out, reps=1, err=None, stream=None):
            None, "mf_contract_probe")
 
 
+def vec_dots(V, x, out, w=None, stream=None):
+    """out[i] = sum_j w[j] V[i, j] x[j] (mf_vec_dots): V a device float64
+    [m, n] tensor (rows are the vectors), x [n], w [n] or None, out [m]."""
+    m, n = int(V.shape[0]), int(V.shape[1])
+    _check(_lib.load().mf_vec_dots(n, _ptr(V), int(V.stride(0)), m, _ptr(x), _ptr(w) if w is not None else None,
+                                   _ptr(out), _stream(stream)), None, "mf_vec_dots")
+
+
+def vec_maxpy(V, c, y, sign=1.0, stream=None):
+    """y += sign sum_i c[i] V[i] (mf_vec_maxpy): V device float64 [m, n], c [m] device."""
+    m, n = int(V.shape[0]), int(V.shape[1])
+    _check(_lib.load().mf_vec_maxpy(n, _ptr(V), int(V.stride(0)), m, _ptr(c), float(sign), _ptr(y),
+                                    _stream(stream)), None, "mf_vec_maxpy")
+
+
+def vec_axpby(a, x, b, y, stream=None):
+    """y = a x + b y (mf_vec_axpby), float64 device vectors."""
+    _check(_lib.load().mf_vec_axpby(int(x.numel()), float(a), _ptr(x), float(b), _ptr(y), _stream(stream)),
+           None, "mf_vec_axpby")
+
+
+def vec_mul(d, v, z, stream=None):
+    """z = d * v entrywise (mf_vec_mul), float64 device vectors."""
+    _check(_lib.load().mf_vec_mul(int(v.numel()), _ptr(d), _ptr(v), _ptr(z), _stream(stream)), None, "mf_vec_mul")
+
+
 def _host_f64(a):
     if hasattr(a, "detach"):
         a = a.detach().cpu().numpy()

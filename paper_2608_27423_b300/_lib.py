@@ -24,7 +24,8 @@ EXPORTS = ["mf_mesh_from_arrays", "mf_mesh_free", "mf_mesh_params_defaults", "mf
            "mf_mg_interpolate", "mf_solve_step_static", "mf_batch_create", "mf_batch_destroy",
            "mf_batch_apply_jacobian", "mf_batch_solve_step", "mf_batch_last_error", "mf_autotune", "mf_set_cells_per_block", "mf_kinetic_energy", "mf_energy", "mf_wall_loads", "mf_run_transient", "mf_fma_peak",
            "mf_mesh_slab", "mf_halo_pack", "mf_halo_add", "mf_mesh_from_arrays_ex",
-           "mf_asm_setup", "mf_asm_apply", "mf_contract_probe"]
+           "mf_asm_setup", "mf_asm_apply", "mf_contract_probe", "mf_vec_dots", "mf_vec_maxpy", "mf_vec_axpby",
+           "mf_vec_mul"]
 PROF_KINDS = ["cell_jac_fp64", "cell_jac_fp32", "mortar_fp64", "mortar_fp32", "cell_residual",
               "cell_linearization", "dirichlet", "diagonal"]
 
@@ -156,6 +157,10 @@ def load():
     lib.mf_profile_read.argtypes = [vp, C.POINTER(MfProfile)]
     lib.mf_fma_peak.argtypes = [i32, C.POINTER(dbl), C.POINTER(dbl), vp]
     lib.mf_contract_probe.argtypes = [i32, i32, i32, vp, vp, vp, vp]
+    lib.mf_vec_dots.argtypes = [i64, vp, i64, i32, vp, vp, vp, vp]
+    lib.mf_vec_maxpy.argtypes = [i64, vp, i64, i32, vp, dbl, vp, vp]
+    lib.mf_vec_axpby.argtypes = [i64, dbl, vp, dbl, vp, vp]
+    lib.mf_vec_mul.argtypes = [i64, vp, vp, vp, vp]
     lib.mf_mesh_slab.argtypes = [vp, i32, i32, C.POINTER(vp), C.POINTER(MfSlabInfo), vp, vp, vp, vp, vp]
     lib.mf_halo_pack.argtypes = [vp, vp, i64, i32, vp, vp]
     lib.mf_asm_setup.argtypes = [vp, C.POINTER(i32), vp]

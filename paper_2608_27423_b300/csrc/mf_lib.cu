@@ -823,6 +823,7 @@ extern "C" mf_status mf_profile_read(mf_handle h, mf_profile_t* out) {
 #include "mf_autotune.inc"
 #include "mf_probe.inc"
 #include "mf_tc.inc"
+#include "mf_vec.inc"
 
 // ---------------------------------------------------------------- batched instances
 struct mf_batch {

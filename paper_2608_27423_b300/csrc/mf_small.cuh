@@ -235,6 +235,26 @@ __global__ void k_mdot_part(int64_t n, const T* __restrict__ V, int64_t ldv, con
     if (threadIdx.x == 0) part[(int64_t)i * gridDim.x + blockIdx.x] = s;
   }
 }
+// Weighted partial dot products: part[i][blockIdx.x] = sum over the block's
+// range of wt[j] V_i[j] x[j] (wt may be null: weights 1); FP64 throughout.
+__global__ void k_wdot_part(int64_t n, const double* __restrict__ V, int64_t ldv, const double* __restrict__ x,
+                            const double* __restrict__ wt, double* __restrict__ part) {
+  const int i = blockIdx.y;
+  const double* v = V + (int64_t)i * ldv;
+  double s = 0.0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    s = fma(wt ? wt[j] * v[j] : v[j], x[j], s);
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[(int64_t)i * gridDim.x + blockIdx.x] = s;
+  }
+}
+
 // Short vectors: out[i] = V_i . w with one block per vector (no second pass);
 // four independent accumulators per thread keep four loads in flight.  Any
 // block size that is a multiple of 32, up to 1024.

@@ -63,3 +63,52 @@ def test_slab_parts_with_device_exchange_equal_global_apply(n_parts):
             got = p[key].cpu().numpy()
             err = np.abs(got - full[p["ng"]]).max() / scale
             assert err <= 1e-12, (key, err)
+
+
+def test_fgmres_with_library_vector_kernels_on_one_part():
+    """The z-slab FGMRES (paper_2608_27423_b300.slab.distributed_fgmres) on a
+    single part, its vector arithmetic in the library's kernels (mf_vec_*),
+    the apply and diagonal of a SlabOperator: after 40 iterations of
+    GMRES(20) (one restart) the residual it reports is the true residual of
+    the oracle's assembled Jacobian, and the iterate equals the same
+    algorithm run on the host with the oracle's apply (tests/test_slab_partition.py
+    runs that one over 1, 2 and 3 gloo ranks)."""
+    from oracle.solve import Operator
+    from paper_2608_27423_b300 import vec_mul
+    from paper_2608_27423_b300.slab import SlabOperator, LibVec, distributed_fgmres
+    mesh, prm, f = synth.make_config(d=3, k=2, m=2, n_r=1, n_s=2, n_z=5, nu=0.05, omega=1.0, dt=0.01, bdf=2,
+                                     theta=0.37, state="smooth", seed=31)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    so = SlabOperator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"], 1, 0)
+    so.set_history(T(f["u_n"]), T(f["u_nm1"]))
+    so.set_linearization(T(f["up_star"]), prm["theta"])
+    n, nf = mesh.n_nodes, mesh.d + 1
+    diag = torch.empty((n, nf), dtype=torch.float64, device="cuda")
+    so.diagonal(diag)
+    dinv = (1.0 / diag).reshape(-1)
+
+    def apply(v, o):
+        so.apply_jacobian(v.view(n, nf), o.view(n, nf))
+
+    def precond(v, o):
+        vec_mul(dinv, v, o)
+
+    b = T(f["x"]).reshape(-1)
+    x = torch.full_like(b, float("nan"))
+    its, res = distributed_fgmres(apply, precond, b, x, None, LibVec, m=20, rtol=1e-14, max_iters=40)
+    assert its == 40
+    ref = Operator(mesh, prm["nu"], prm["omega"], prm["dt"], prm["bdf"], prm["theta"], up_star=f["up_star"],
+                   u_n=f["u_n"], u_nm1=f["u_nm1"])
+    J = ref.assemble().tocsr()
+    xh = x.cpu().numpy()
+    bh = np.asarray(f["x"]).reshape(-1)
+    true_res = np.linalg.norm(bh - J @ xh) / np.linalg.norm(bh)
+    assert abs(res - true_res) <= 1e-7 * true_res
+    # the same algorithm on the host with the oracle's apply and diagonal
+    from paper_2608_27423_b300.slab import distributed_fgmres as fg
+    from tests.test_slab_partition import _TorchVec
+    dref = torch.tensor(np.asarray(J.diagonal()).copy())
+    xr = torch.zeros(n * nf, dtype=torch.float64)
+    fg(lambda v, o: o.copy_(torch.tensor(J @ v.numpy())), lambda v, o: o.copy_(v / dref),
+       torch.tensor(bh.copy()), xr, None, _TorchVec, m=20, rtol=1e-14, max_iters=40)
+    assert np.abs(xh - xr.numpy()).max() <= 1e-8 * np.abs(xr.numpy()).max()
