@@ -102,6 +102,37 @@ __global__ void k_cast(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
 // Cell part of diag(J): for each local DoF (node a, field f) the entry of the
 // element matrix of blocks A-hat (velocity) and D-hat (pressure) on the
 // diagonal, summed over the Gauss points from the linearisation cache.
+// The cache fields the diagonal reads at each point (slot order: J^-1, W, G,
+// ctil, a, the diagonal of grad u*, tau, R*) and their count.
+template <int D> struct DiagSlots {
+  static constexpr int n = D * D + 1 + Sym<D>::n + 3 * D + 1 + D;
+  __device__ static int field(int s) {
+    using CF = Cache<D>;
+    if (s < D * D) return CF::JINV + s;
+    s -= D * D;
+    if (s == 0) return CF::W;
+    s -= 1;
+    if (s < Sym<D>::n) return CF::G + s;
+    s -= Sym<D>::n;
+    if (s < D) return CF::CT + s;
+    s -= D;
+    if (s < D) return CF::A + s;
+    s -= D;
+    if (s < D) return CF::GU + s * D + s;
+    s -= D;
+    if (s == 0) return CF::TAU;
+    return CF::RS + (s - 1);
+  }
+};
+// Every node's thread needs every point's coefficients of its cell: where the
+// block's share fits (FP32, and FP64 at small k) they are staged in shared
+// memory once, coalesced, instead of re-read NQ times per cell from L1/L2.
+template <int D, int K, typename T> struct DiagCfg {
+  static constexpr int BYTES = CellCfg<D, K>::CPB * DiagSlots<D>::n * CellCfg<D, K>::NQ * (int)sizeof(T);
+  static constexpr bool STAGE = BYTES <= 40 * 1024;
+  static constexpr int CPB_S = STAGE ? CellCfg<D, K>::CPB : 1, NQ_S = STAGE ? CellCfg<D, K>::NQ : 1;
+};
+
 template <int D, int K, typename T>
 __global__ void __launch_bounds__(CellCfg<D, K>::THREADS)
 k_cell_diag(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__ cache, T* __restrict__ diag,
@@ -109,14 +140,25 @@ k_cell_diag(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__
   using C = CellCfg<D, K>;
   constexpr int N = C::N, NQ = C::NQ, NF = D + 1;
   using CF = Cache<D>;
+  using DS = DiagSlots<D>;
+  using G = DiagCfg<D, K, T>;
   __shared__ SmTab<N, T> st;
+  __shared__ T sc[G::CPB_S][DS::n][G::NQ_S];
   load_tab<K, T>(st);
+  const int64_t P = nc * NQ;
+  if constexpr (G::STAGE) {
+    const int64_t c0 = (int64_t)blockIdx.x * C::CPB;
+    for (int i = threadIdx.x; i < C::CPB * NQ * DS::n; i += blockDim.x) {
+      const int s = i / (C::CPB * NQ), rem = i % (C::CPB * NQ);
+      const int c = rem / NQ, q = rem % NQ;
+      sc[c][s][q] = (c0 + c < nc) ? cache[(int64_t)DS::field(s) * P + c0 * NQ + rem] : T(0);
+    }
+  }
   __syncthreads();
   const int cl = threadIdx.x / NQ, t = threadIdx.x % NQ;
   const int64_t cell = (int64_t)blockIdx.x * C::CPB + cl;
   if (cell >= nc) return;
   const int ai[3] = {t % N, (t / N) % N, t / (N * N)};
-  const int64_t P = nc * NQ;
   T dsum[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) dsum[f] = T(0);
@@ -146,13 +188,19 @@ k_cell_diag(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__
       for (int u = 0; u < D; ++u) p *= (r == s) ? (u == r ? hv[u] : bv[u]) : ((u == r || u == s) ? dvv[u] : bv[u]);
       Hphi[e] = p;
     }
-    const T* cp = cache + cell * NQ + q;
+    // slot s of this point: the staged copy, else the cache itself
+    auto fv = [&](int s) -> T {
+      if constexpr (G::STAGE) return sc[cl][s][q];
+      else return cache[(int64_t)DS::field(s) * P + cell * NQ + q];
+    };
+    constexpr int SW = D * D, SG = SW + 1, SCT = SG + Sym<D>::n, SA = SCT + D, SGU = SA + D, STAU = SGU + D,
+                  SRS = STAU + 1;
     T Ji[D][D];
 #pragma unroll
     for (int r = 0; r < D; ++r)
 #pragma unroll
-      for (int m = 0; m < D; ++m) Ji[r][m] = cp[(CF::JINV + r * D + m) * P];
-    const T Wq = cp[CF::W * P];
+      for (int m = 0; m < D; ++m) Ji[r][m] = fv(r * D + m);
+    const T Wq = fv(SW);
     T gphi[D];
 #pragma unroll
     for (int m = 0; m < D; ++m) {
@@ -163,18 +211,18 @@ k_cell_diag(const int32_t* __restrict__ cells, int64_t nc, const T* __restrict__
     }
     T lap = T(0);
 #pragma unroll
-    for (int e = 0; e < Sym<D>::n; ++e) lap = fma(cp[(CF::G + e) * P], Hphi[e], lap);
+    for (int e = 0; e < Sym<D>::n; ++e) lap = fma(fv(SG + e), Hphi[e], lap);
 #pragma unroll
-    for (int r = 0; r < D; ++r) lap = fma(-cp[(CF::CT + r) * P], dphi[r], lap);
+    for (int r = 0; r < D; ++r) lap = fma(-fv(SCT + r), dphi[r], lap);
     T sa = T(0), g2 = T(0);
 #pragma unroll
-    for (int m = 0; m < D; ++m) { sa = fma(cp[(CF::A + m) * P], gphi[m], sa); g2 = fma(gphi[m], gphi[m], g2); }
-    const T tau = cp[CF::TAU * P];
+    for (int m = 0; m < D; ++m) { sa = fma(fv(SA + m), gphi[m], sa); g2 = fma(gphi[m], gphi[m], g2); }
+    const T tau = fv(STAU);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      const T guc = cp[(CF::GU + c * D + c) * P];
+      const T guc = fv(SGU + c);
       const T lb = a0dt * phi + sa + guc * phi;
-      T e = phi * lb + nu * g2 + tau * sa * (lb - nu * lap) + tau * phi * gphi[c] * cp[(CF::RS + c) * P];
+      T e = phi * lb + nu * g2 + tau * sa * (lb - nu * lap) + tau * phi * gphi[c] * fv(SRS + c);
       dsum[c] = fma(Wq, e, dsum[c]);
     }
     dsum[D] = fma(Wq * tau, g2, dsum[D]);
