@@ -409,6 +409,8 @@ typedef struct {
   double step_rtol;       /* mf_run_transient only: > 0 turns on per-step convergence control (after
                              newton_iters iterations, one more at a time, up to max_newton per step,
                              while ||R|| > step_rtol ||R_0|| of the step); 0 = fixed iterations (default) */
+  int    smooth_cgs_passes; /* MF_PC_MG: classical Gram-Schmidt passes of the smoothing GMRES on every
+                               level, 1 or 2 (default 2); the coarse solve always takes 2 */
 } mf_solver_opts;
 
 typedef struct {

@@ -52,7 +52,8 @@ class MfSolverOpts(C.Structure):
                 ("cheb_lo", C.c_double), ("theta", C.c_double), ("inner_iters", C.c_int),
                 ("line_search", C.c_int), ("mg_smooth", C.c_int), ("mg_coarse_iters", C.c_int),
                 ("deflate_pressure", C.c_int), ("use_graphs", C.c_int), ("outer_precision", C.c_int),
-                ("batch_fallback", C.c_int), ("mg_smoother", C.c_int), ("step_rtol", C.c_double)]
+                ("batch_fallback", C.c_int), ("mg_smoother", C.c_int), ("step_rtol", C.c_double),
+                ("smooth_cgs_passes", C.c_int)]
 
 
 class MfSolveReport(C.Structure):

@@ -119,6 +119,7 @@ struct mf_ctx {
   int64_t nmwall = 0;  // the last nmwall entries of `wall` move with the rotor (blade walls)
   bool have_lin = false;
   bool geo_valid = false;              // the cache's geometry fields match the current coordinates
+  int smooth_passes = 2;               // Gram-Schmidt passes of this level's smoothing GMRES (solver option)
   bool angle_set = false;              // coordinates, mortar map and face geometry are at the host angle `theta`
   int ncache = 0;
   int nb = 0;  // blocks for reductions
