@@ -264,3 +264,26 @@ def test_distributed_fgmres_matches_single_part():
     scale = np.abs(xs[1]).max()
     for world in (2, 3):
         assert np.abs(xs[world] - xs[1]).max() <= 1e-9 * scale, world
+
+
+@pytest.mark.parametrize("n_parts", [2, 3, 5])
+def test_owned_weights_count_every_global_row_once(n_parts):
+    """The weights of the parts' dot products (owned_weights): summed over the
+    parts through node_global they are 1 on every global row, so a weighted
+    local dot product all-reduced over the parts is the global one."""
+    from paper_2608_27423_b300 import slab_partition
+    from paper_2608_27423_b300.slab import owned_weights
+    mesh, prm, f = _mesh()
+    nf = mesh.d + 1
+    total = np.zeros((mesh.n_nodes, nf))
+    rng = np.random.default_rng(3)
+    a, b = rng.uniform(-1, 1, (2, mesh.n_nodes, nf))
+    dot = 0.0
+    for p in range(n_parts):
+        _, plan = slab_partition(mesh, n_parts, p)
+        ng = plan["node_global"]
+        w = owned_weights(plan, len(ng), nf).numpy().reshape(len(ng), nf)
+        np.add.at(total, ng, w)
+        dot += float((w * a[ng] * b[ng]).sum())
+    assert np.array_equal(total, np.ones_like(total))
+    assert abs(dot - float((a * b).sum())) <= 1e-12 * abs(float((a * b).sum()))
